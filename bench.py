@@ -1,0 +1,341 @@
+"""Benchmark: wave-LB GLUPS and radiation forces/s on one GB300.
+
+One step = one whole force evaluation of the 3D sphere workload (256^3 D3Q7,
+FP32 populations, lambda = 128, R = 16 at lambda/8, seeded compressibility
+ratio, 2000 Fibonacci points, 30 periods = 15360 LB steps, last 10 averaged):
+setup and initial condition, the unsampled and the sampled periods, and the
+FP64 force, all on the device.  Inputs (two population copies of 470 MB each)
+are far larger than L2, so no flush is needed between steps.
+
+value       GLUPS = cells x LB steps / device time (CUDA events on the
+            library's stream, max over ranks), whole job.
+roofline    the update kernel: algorithmic bytes per launch (57 B per cell:
+            7 + 7 FP32 populations and the class byte) / its average launch
+            time, measured over the unsampled periods of the timed steps.
+e2e         the same metric through the public C ABI from host parameters to
+            host force: handle creation on a torch workspace, wlb_run, read-back.
+cpu_baseline  the FP64 oracle on the host cores, a bounded sample of the same
+            lattice (a few LB steps with sampling), as GLUPS.
+
+--impl reference times the oracle alone (the paper has no code to run).
+N > 1 (torchrun): independent replicas, one lattice per rank ("replicas only").
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "3D sphere 256^3 D3Q7 FP32, lambda=128, R=16 at lambda/8, 2000 Fibonacci points, 30 periods avg last 10"
+METRIC = "wave-LB GLUPS (% HBM roofline); radiation forces/s at <=1% err vs FP64 oracle"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _traffic(kernel_src_sha):
+    """Per-launch DRAM bytes of the update kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "update_rows_d3q7_f32_256cubed.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_src_sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def _kernel_sha():
+    src = os.path.join(ROOT, "paper_2404_02346_gb300", "csrc", "wlb_step.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(prob, target_s=15.0, steps=None):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
+    the full lattice for a few LB steps, a third of them sampled."""
+    import oracle
+    oracle.build.build()
+    if steps is None:
+        probe = dict(prob, n_steps=3, n_window=1)
+        t0 = time.perf_counter()
+        oracle.run(probe)
+        t_probe = time.perf_counter() - t0
+        steps = max(3, min(60, int(3 * target_s / max(t_probe, 1e-3))))
+        steps -= steps % 3
+    sample = dict(prob, n_steps=steps, n_window=steps // 3)
+    t0 = time.perf_counter()
+    oracle.run(sample)
+    dt = time.perf_counter() - t0
+    cells = prob["n"][0] * prob["n"][1] * prob["n"][2]
+    return {"value": cells * steps / dt / 1e9, "unit": "GLUPS", "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": "%d LB steps (%d sampled) of the %dx%dx%d lattice incl. setup, %.1f s"
+                      % (steps, steps // 3, *prob["n"], dt)}
+
+
+def run_reference(args, prob):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build.build()
+    cells = prob["n"][0] * prob["n"][1] * prob["n"][2]
+    per_step = 6  # LB steps per bench step: bounded so K + W steps take minutes
+    sample = dict(prob, n_steps=per_step, n_window=per_step // 3)
+    for _ in range(args.warmup):
+        oracle.run(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(sample)
+    dt = time.perf_counter() - t0
+    value = cells * per_step * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (oracle: %d LB steps per step)" % per_step,
+                   "l2": "inputs larger than L2"},
+        "cpu_baseline": {"kind": "oracle", "cores": oracle.threads(), "value": value, "unit": "GLUPS",
+                         "sample": "%d LB steps of the 256^3 lattice per step, setup included" % per_step},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, prob):
+    import ctypes
+
+    import torch
+
+    import paper_2404_02346_gb300 as wlb
+    from paper_2404_02346_gb300 import build as B
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.build()
+    stream = torch.cuda.Stream()
+    cells = prob["n"][0] * prob["n"][1] * prob["n"][2]
+    solver = wlb.Solver(prob, stream=stream)
+    info = solver.info()
+    n_steps, n_window = info.n_steps, info.n_window
+    n_free = n_steps - n_window
+    n_avg = n_window // info.period
+
+    def one_step(ev=None):
+        solver.init()
+        if ev is not None:
+            ev[0].record(stream)
+        solver.step(n_free, sample=False)
+        if ev is not None:
+            ev[1].record(stream)
+        solver.step(n_window, sample=True)
+        return solver.force()
+
+    for _ in range(args.warmup):
+        F = one_step()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    k1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    start.record(stream)
+    for i in range(args.steps):
+        F = one_step(k1[i])
+    end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    k1_ms = sum(a.elapsed_time(b) for a, b in k1) / (args.steps * n_free)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    lu = cells * n_steps * args.steps * world
+    glups = lu / (ms * 1e-3) / 1e9
+    forces_per_s = args.steps * world / (ms * 1e-3)
+
+    # end to end through the public API: host parameters in, host force out
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Fe = wlb.compute_force(prob)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": cells * n_steps * e2e_steps * world / e2e_s / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": ctypes.sizeof(wlb.Params), "d2h_bytes_per_step": 4 * 8 + 4,
+           "forces_per_s": e2e_steps / e2e_s, "force": [float(v) for v in Fe]}
+
+    peaks = _peaks()
+    bpu = info.bytes_per_update
+    achieved = bpu * cells / (k1_ms * 1e-3) / 1e9
+    if peaks and "hbm_gbs" in peaks:
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    traffic = _traffic(_kernel_sha())
+    launches = args.steps * (2 + n_free + 2 * n_window + n_avg + 1)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells, "lb_steps_per_force": n_steps,
+                       "window_steps": n_window, "kappa_ratio": prob.get("kappa"),
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs (2 x 470 MB populations) larger than L2; no flush"},
+            "forces_per_s": forces_per_s,
+            "force": [float(v) for v in F],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "update_rows<float,3,2>", "bytes_per_cell": bpu,
+                         "avg_launch_us": k1_ms * 1e3, "peak_source": peak_src + " hbm_gbs"},
+            "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(prob)
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_profile(args, prob):
+    """A short pass over the benchmark lattice for ncu: setup, 64 unsampled and
+    64 sampled steps (graph-replayed where whole periods allow), the force."""
+    import torch
+
+    import paper_2404_02346_gb300 as wlb
+    from paper_2404_02346_gb300 import build as B
+
+    B.build()
+    stream = torch.cuda.Stream()
+    with wlb.Solver(prob, stream=stream) as s:
+        s.init()
+        s.step(args.profile_steps, sample=False)
+        s.step(args.profile_steps, sample=True)
+        F = s.force()
+    print(json.dumps({"profile_run": True, "force": [float(v) for v in F],
+                      "launches": 2 + 3 * args.profile_steps + 2}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="short pass for ncu captures")
+    ap.add_argument("--profile-steps", type=int, default=64)
+    args = ap.parse_args()
+    prob = workloads.sphere_3d(seed=args.seed)
+    if args.profile:
+        run_profile(args, prob)
+    elif args.impl == "reference":
+        run_reference(args, prob)
+    else:
+        run_gpu(args, prob)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * wlb.h - C ABI of the GB300 wave lattice Boltzmann acoustic-radiation-force
+ * library (sm_103a).
+ *
+ * The library computes the time-averaged acoustic radiation force on a
+ * density-matched compressible object held in a standing acoustic wave, by the
+ * method of Castro-Avila, Malgaretti, Harting and Munoz, "A lattice Boltzmann
+ * approach for acoustic manipulation":
+ *
+ *   1. a wave lattice Boltzmann model (D2Q5 or D3Q7, BGK with tau = 1/2,
+ *      Sec. V, Eqs. 62-64 and 71) marches the first-order fields p1 and u1 on a
+ *      lattice whose sound speed c(x) carries the object (Sec. VI, Eq. 79);
+ *   2. p1 and u1 are interpolated onto N surface points with the three-point
+ *      kernel of Eq. (82) (Eqs. 80-81) and time-averaged as <p1^2>, <u1.u1> and
+ *      <u1 (u1.n)> over the last n_avg_periods periods (Sec. VII);
+ *   3. King's surface integral, Eq. (14) (Eq. 77 in lattice variables), gives
+ *      the force in FP64.
+ *
+ * All lattice quantities are in lattice units (dx = dt = 1).  The lattice is
+ * periodic on every axis.  The initial condition is the standing wave
+ * p1 = p_a cos(2 pi (s - antinode) / wavelength), u1 = 0, imposed through the
+ * equilibrium as Eq. (72) describes for initial conditions.
+ *
+ * Conventions
+ *   - Every call returns a wlb_status and never aborts the process.
+ *   - Host pointers are owned by the caller.  Device memory is owned by the
+ *     handle: either one caller-provided device workspace (see
+ *     wlb_workspace_bytes) or, when none is given, memory the library allocates
+ *     with cudaMalloc in wlb_create and frees in wlb_destroy.
+ *   - Work is issued asynchronously on the CUDA stream given to wlb_create;
+ *     calls that return host data (wlb_force, wlb_fields, wlb_surface,
+ *     wlb_mask, wlb_run) synchronise that stream before returning.
+ *   - A handle is not thread safe; distinct handles are independent.
+ *   - Population layout in device memory: structure of arrays f[i][z][y][x],
+ *     x fastest, velocity order i = 0 (rest), +x, -x, +y, -y, +z, -z.
+ */
+#ifndef WLB_H
+#define WLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WLB_OK = 0,
+    WLB_ERR_ARG = 1,       /* invalid parameter or argument                    */
+    WLB_ERR_UNSTABLE = 2,  /* non-finite time-average accumulators              */
+    WLB_ERR_CUDA = 3,      /* a CUDA runtime call or kernel launch failed       */
+    WLB_ERR_OOM = 4,       /* device or host allocation failed, or workspace too small */
+    WLB_ERR_STATE = 5      /* call out of order (e.g. wlb_step before wlb_init) */
+} wlb_status;
+
+typedef enum { WLB_D2Q5 = 0, WLB_D3Q7 = 1 } wlb_lattice;          /* Fig. 8   */
+typedef enum { WLB_POP_F32 = 0, WLB_POP_F64 = 1 } wlb_precision;  /* storage and arithmetic of the populations */
+
+/*
+ * Problem statement (Sec. VII and Table I; Eq. 79 for the object).
+ *
+ *   lattice        WLB_D2Q5 (2D, nz must be 1) or WLB_D3Q7.
+ *   nx, ny, nz     lattice extents; all axes periodic.
+ *   wave_axis      0, 1 or 2: axis s of the standing wave.
+ *   c0, cp         sound speed of fluid and object; stability needs
+ *                  D c^2 < 1 for both (D = 2 or 3; it keeps f_0^eq >= 0).
+ *   rho0           mean density (the object is density matched).
+ *   p_a            pressure amplitude of the standing wave.
+ *   wavelength     lambda in cells; the box along wave_axis must hold a whole
+ *                  number of wavelengths and T = lambda / c0 must be a whole
+ *                  number of steps.
+ *   antinode       coordinate of a pressure antinode along wave_axis.
+ *   center         object centre r0 (the z entry is ignored in 2D).  Exact
+ *                  integer classification of cells needs |x - r0|^2 exact in
+ *                  double precision: use multiples of 2^-10.
+ *   radius         R_p.
+ *   interface_d    "square thickness" d of Eq. (79) (the paper uses 4).
+ *   surface_radius radius of the integration surface (R_p in the paper).
+ *   n_surface      N surface elements: equal arcs in 2D, Fibonacci points in 3D.
+ *   n_periods      total run length in periods T.
+ *   n_avg_periods  the last n_avg_periods periods are averaged (<= n_periods).
+ *   precision      WLB_POP_F32 or WLB_POP_F64.
+ *
+ * The object, its interface band and the interpolation stencil must fit in
+ * half the box along every axis (minimum-image distances must be unique).
+ */
+typedef struct {
+    int lattice;
+    int nx, ny, nz;
+    int wave_axis;
+    double c0, cp, rho0;
+    double p_a, wavelength, antinode;
+    double center[3];
+    double radius, interface_d, surface_radius;
+    int n_surface;
+    int n_periods, n_avg_periods;
+    int precision;
+} wlb_params;
+
+typedef struct wlb_handle wlb_handle;
+
+/* Sizes derived from a parameter set. */
+typedef struct {
+    int dim, q;                 /* 2 or 3; 5 or 7 populations                   */
+    long long cells;            /* nx * ny * nz                                 */
+    long long period;           /* T = wavelength / c0 steps                    */
+    long long n_steps;          /* n_periods * T                                */
+    long long n_window;         /* n_avg_periods * T                            */
+    long long steps_done;       /* steps since the last wlb_init (0 if none)    */
+    long long samples_done;     /* steps sampled since the last wlb_init        */
+    double bytes_per_update;    /* algorithmic HBM bytes of one cell update:
+                                   2 q pop_bytes + 1 (class byte)              */
+    int vector_path;            /* 1 if the row-vectorised update kernel is used */
+} wlb_info;
+
+/* Check a parameter set.  WLB_ERR_ARG for: unknown lattice or precision,
+ * non-positive sizes, nz != 1 in 2D, bad wave_axis, D c0^2 >= 1 or
+ * D cp^2 >= 1, c0 <= 0, cp <= 0, rho0 <= 0, non-integral T = wavelength/c0,
+ * a box length along wave_axis that is not a whole number of wavelengths,
+ * radius <= 0, interface_d <= 0, an object + band + stencil wider than half
+ * the box, n_surface < 0, n_periods < 1, n_avg_periods outside [0, n_periods]. */
+wlb_status wlb_validate(const wlb_params *p);
+
+/* Device workspace, in bytes, that wlb_create needs for these parameters. */
+wlb_status wlb_workspace_bytes(const wlb_params *p, size_t *bytes);
+
+/* Create a handle.  device_workspace: NULL to let the library cudaMalloc its
+ * own memory, else a device pointer (256-byte aligned) to at least
+ * wlb_workspace_bytes bytes that stays valid until wlb_destroy.  stream: a
+ * cudaStream_t (NULL = legacy default stream) on which all work is issued.
+ * Captures nothing and launches nothing.  *out is set only on WLB_OK. */
+wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t workspace_bytes,
+                      void *stream, wlb_handle **out);
+
+/* Setup and initial condition (asynchronous): cell classes and sound-speed
+ * field (Eq. 79), surface elements and interpolation weights (Sec. VI,
+ * Eqs. 80-82), the standing wave imposed through the equilibrium (Eq. 72),
+ * and zeroed time averages.  Resets the step and sample counters. */
+wlb_status wlb_init(wlb_handle *h);
+
+/* Advance n_steps >= 0 lattice steps (asynchronous).  Each step streams and
+ * collides every cell (Eqs. 62-64, 71).  sample != 0 adds, at each step and
+ * before its collision, the surface interpolation and the running sums of
+ * p1^2, u1.u1 and (n.u1) u1 (Eqs. 80-82); FP32 running sums (FP64 with
+ * WLB_POP_F64) are folded into FP64 once per period.  Whole periods are
+ * replayed as CUDA graphs captured on first use.  WLB_ERR_STATE before
+ * wlb_init. */
+wlb_status wlb_step(wlb_handle *h, long long n_steps, int sample);
+
+/* Time-averaged force from the samples taken since wlb_init, Eq. (14) in
+ * FP64:  F_i = - sum_k dS_k [ (<p1^2>/(2 rho0 c0^2) - rho0 <u1.u1>/2) n_ki
+ *                              + rho0 <u1_i (u1.n_k)> ].
+ * Writes 3 doubles to force_out (host; the third is 0 in 2D) and
+ * synchronises.  All zero if nothing was sampled.  WLB_ERR_UNSTABLE if any
+ * accumulator is not finite. */
+wlb_status wlb_force(wlb_handle *h, double force_out[3]);
+
+/* The whole protocol: wlb_init, (n_periods - n_avg_periods) T unsampled steps,
+ * n_avg_periods T sampled steps, wlb_force. */
+wlb_status wlb_run(wlb_handle *h, double force_out[3]);
+
+/* Fields at the current time: p1 = c^2 rho1 and u1 = J1 / rho0 (Eq. 62).
+ * p1_out: nx*ny*nz doubles, u1_out: dim*nx*ny*nz doubles laid out
+ * [a][z][y][x]; either may be NULL.  Host buffers; synchronises. */
+wlb_status wlb_fields(wlb_handle *h, double *p1_out, double *u1_out);
+
+/* Surface elements after wlb_init: n_surface rows of
+ * (x, y, z, n_x, n_y, n_z, dS) doubles (host buffer); synchronises. */
+wlb_status wlb_surface(wlb_handle *h, double *pts_out);
+
+/* Cell classes after wlb_init: nx*ny*nz bytes [z][y][x] (host buffer):
+ * 0 fluid (c = c0), 1 object (c = cp), 2 interface band (c from Eq. 79).
+ * A cell is fluid when (|x - r0|^2 - R_p^2) >= 20 d, object when it is
+ * <= -20 d, band otherwise (minimum-image distance); beyond the band the tanh
+ * of Eq. (79) is +-1 in double precision.  Synchronises. */
+wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out);
+
+/* Sizes and counters of a handle. */
+wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
+
+/* Release the handle, its graphs, streams and any memory it allocated. */
+wlb_status wlb_destroy(wlb_handle *h);
+
+/* Static description of a status code. */
+const char *wlb_status_str(wlb_status s);
+
+/* Detail of the last error on this handle ("" if none). */
+const char *wlb_last_error(const wlb_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WLB_H */

@@ -1,0 +1,224 @@
+"""GB300 wave lattice Boltzmann acoustic-radiation-force library: Python binding.
+
+Argument marshalling only.  Every step of the computation runs in the CUDA
+library ``_build/libwlb.so`` behind the C ABI of ``include/wlb.h``; PyTorch
+supplies the device workspace and the CUDA stream.  There is no CPU path: if
+the library has not been built, importing the binding's entry points raises.
+
+Names follow ``include/wlb.h``: ``Solver.init/step/force/run/fields/surface/
+mask/info`` wrap ``wlb_init/wlb_step/...``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwlb.so")
+
+WLB_OK, WLB_ERR_ARG, WLB_ERR_UNSTABLE, WLB_ERR_CUDA, WLB_ERR_OOM, WLB_ERR_STATE = range(6)
+WLB_D2Q5, WLB_D3Q7 = 0, 1
+WLB_POP_F32, WLB_POP_F64 = 0, 1
+
+
+class WlbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``wlb_params``."""
+    _fields_ = [
+        ("lattice", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("wave_axis", ctypes.c_int),
+        ("c0", ctypes.c_double), ("cp", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("p_a", ctypes.c_double), ("wavelength", ctypes.c_double), ("antinode", ctypes.c_double),
+        ("center", ctypes.c_double * 3),
+        ("radius", ctypes.c_double), ("interface_d", ctypes.c_double),
+        ("surface_radius", ctypes.c_double),
+        ("n_surface", ctypes.c_int),
+        ("n_periods", ctypes.c_int), ("n_avg_periods", ctypes.c_int),
+        ("precision", ctypes.c_int),
+    ]
+
+
+class Info(ctypes.Structure):
+    """Mirror of ``wlb_info``."""
+    _fields_ = [
+        ("dim", ctypes.c_int), ("q", ctypes.c_int),
+        ("cells", ctypes.c_longlong), ("period", ctypes.c_longlong),
+        ("n_steps", ctypes.c_longlong), ("n_window", ctypes.c_longlong),
+        ("steps_done", ctypes.c_longlong), ("samples_done", ctypes.c_longlong),
+        ("bytes_per_update", ctypes.c_double), ("vector_path", ctypes.c_int),
+    ]
+
+
+_lib = None
+# Functions declared in include/wlb.h, with their ctypes signatures.
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_SIGNATURES = {
+    "wlb_validate": (ctypes.c_int, [ctypes.POINTER(Params)]),
+    "wlb_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]),
+    "wlb_create": (ctypes.c_int, [ctypes.POINTER(Params), _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "wlb_init": (ctypes.c_int, [_VP]),
+    "wlb_step": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_int]),
+    "wlb_force": (ctypes.c_int, [_VP, _DP]),
+    "wlb_run": (ctypes.c_int, [_VP, _DP]),
+    "wlb_fields": (ctypes.c_int, [_VP, _DP, _DP]),
+    "wlb_surface": (ctypes.c_int, [_VP, _DP]),
+    "wlb_mask": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ubyte)]),
+    "wlb_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(Info)]),
+    "wlb_destroy": (ctypes.c_int, [_VP]),
+    "wlb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "wlb_last_error": (ctypes.c_char_p, [_VP]),
+}
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("CUDA library not built: %s (run __graft_entry__.build())" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, handle=None, what=""):
+    if status != WLB_OK:
+        L = lib()
+        detail = L.wlb_last_error(handle).decode() if handle else ""
+        raise WlbError(status, "%s: %s %s" % (what, L.wlb_status_str(status).decode(), detail))
+
+
+def params_from_problem(prob, precision=None):
+    """wlb_params from a problem dictionary (see workloads.py)."""
+    p = Params()
+    dim = int(prob["dim"])
+    p.lattice = WLB_D2Q5 if dim == 2 else WLB_D3Q7
+    n = list(prob["n"]) + [1] * (3 - len(prob["n"]))
+    p.nx, p.ny, p.nz = (int(v) for v in n[:3])
+    p.wave_axis = int(prob["wave_axis"])
+    for k in ("c0", "cp", "rho0", "p_a", "wavelength", "antinode", "radius", "interface_d",
+              "surface_radius"):
+        setattr(p, k, float(prob[k]))
+    c = list(prob["center"]) + [0.0] * (3 - len(prob["center"]))
+    for a in range(3):
+        p.center[a] = float(c[a])
+    p.n_surface = int(prob["n_surface"])
+    T = prob["period"] if "period" in prob else int(round(prob["wavelength"] / prob["c0"]))
+    if prob["n_steps"] % T or prob["n_window"] % T:
+        raise ValueError("n_steps and n_window must be whole periods")
+    p.n_periods = int(prob["n_steps"] // T)
+    p.n_avg_periods = int(prob["n_window"] // T)
+    prec = precision or prob.get("precision", "f32")
+    p.precision = WLB_POP_F64 if prec == "f64" else WLB_POP_F32
+    return p
+
+
+def workspace_bytes(params):
+    nb = ctypes.c_size_t()
+    _check(lib().wlb_workspace_bytes(ctypes.byref(params), ctypes.byref(nb)), what="wlb_workspace_bytes")
+    return nb.value
+
+
+def validate(params):
+    return lib().wlb_validate(ctypes.byref(params))
+
+
+class Solver:
+    """One lattice problem on the current CUDA device.
+
+    Device memory is one torch uint8 tensor handed to ``wlb_create``; work is
+    issued on ``stream`` (a torch.cuda.Stream; default: the current stream).
+    """
+
+    def __init__(self, problem, stream=None, precision=None):
+        import torch  # device memory and streams only
+
+        self.problem = problem
+        self.params = params_from_problem(problem, precision)
+        L = lib()
+        nb = workspace_bytes(self.params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ws = torch.empty(nb, dtype=torch.uint8, device=self.stream.device)
+        h = _VP()
+        _check(L.wlb_create(ctypes.byref(self.params), ctypes.c_void_p(self._ws.data_ptr()), nb,
+                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), what="wlb_create")
+        self._h = h
+        info = self.info()
+        self.dim, self.q, self.cells = info.dim, info.q, info.cells
+        self.shape = (self.params.nz, self.params.ny, self.params.nx)
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wlb_destroy(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls -----------------------------------------------------------
+    def info(self):
+        out = Info()
+        _check(lib().wlb_get_info(self._h, ctypes.byref(out)), self._h, "wlb_get_info")
+        return out
+
+    def init(self):
+        _check(lib().wlb_init(self._h), self._h, "wlb_init")
+
+    def step(self, n, sample=False):
+        _check(lib().wlb_step(self._h, int(n), 1 if sample else 0), self._h, "wlb_step")
+
+    def force(self):
+        F = np.zeros(3)
+        _check(lib().wlb_force(self._h, F.ctypes.data_as(_DP)), self._h, "wlb_force")
+        return F
+
+    def run(self):
+        F = np.zeros(3)
+        _check(lib().wlb_run(self._h, F.ctypes.data_as(_DP)), self._h, "wlb_run")
+        return F
+
+    def fields(self):
+        p1 = np.zeros(self.shape)
+        u1 = np.zeros((self.dim,) + self.shape)
+        _check(lib().wlb_fields(self._h, p1.ctypes.data_as(_DP), u1.ctypes.data_as(_DP)), self._h,
+               "wlb_fields")
+        return p1, u1
+
+    def surface(self):
+        pts = np.zeros((max(self.params.n_surface, 1), 7))
+        _check(lib().wlb_surface(self._h, pts.ctypes.data_as(_DP)), self._h, "wlb_surface")
+        return pts[: self.params.n_surface]
+
+    def mask(self):
+        m = np.zeros(self.shape, dtype=np.uint8)
+        _check(lib().wlb_mask(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))), self._h,
+               "wlb_mask")
+        return m
+
+
+def compute_force(problem, precision=None):
+    """One force evaluation through the public API (host in, host out)."""
+    with Solver(problem, precision=precision) as s:
+        return s.run()

@@ -1,0 +1,419 @@
+// Host side of the C ABI declared in include/wlb.h: parameter validation,
+// workspace layout, the step loop (per-period CUDA graphs) and read-back.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/wlb.h"
+#include "wlb_internal.cuh"
+
+using wlb::Buffers;
+using wlb::Geometry;
+
+struct wlb_handle {
+    wlb_params p;
+    Geometry g;
+    Buffers b;
+    bool f64 = false;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;  // private stream used only to capture graphs
+    void *owned = nullptr;           // workspace allocated by the library, if any
+    double *host_out = nullptr;      // pinned: force[4] + error flag
+    int src = 0;                     // population buffer holding the current state
+    bool initialised = false;
+    long long period = 0, n_steps = 0, n_window = 0;
+    long long steps_done = 0, samples_done = 0, samples_in_period = 0;
+    cudaGraphExec_t graph_free[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph_sampled[2] = {nullptr, nullptr};
+    bool vector_path = false;
+    char err[512] = {0};
+};
+
+namespace {
+
+constexpr long long kStageCells = 1LL << 20;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+wlb_status fail(wlb_handle *h, wlb_status s, const char *what, cudaError_t e = cudaSuccess) {
+    if (h) {
+        if (e != cudaSuccess)
+            snprintf(h->err, sizeof(h->err), "%s: %s", what, cudaGetErrorString(e));
+        else
+            snprintf(h->err, sizeof(h->err), "%s", what);
+    }
+    return s;
+}
+
+#define WLB_CUDA(h, call, what)                                   \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return fail((h), WLB_ERR_CUDA, (what), e_); \
+    } while (0)
+
+int dim_of(const wlb_params *p) { return p->lattice == WLB_D2Q5 ? 2 : 3; }
+
+bool whole(double v) { return std::isfinite(v) && v > 0 && std::fabs(v - std::nearbyint(v)) < 1e-9 * std::fmax(1.0, v); }
+
+Geometry make_geometry(const wlb_params *p) {
+    Geometry g{};
+    g.dim = dim_of(p);
+    g.q = 2 * g.dim + 1;
+    g.n[0] = p->nx;
+    g.n[1] = p->ny;
+    g.n[2] = p->nz;
+    g.ncell = (long long)p->nx * p->ny * p->nz;
+    g.wave_axis = p->wave_axis;
+    g.c0 = p->c0;
+    g.cp = p->cp;
+    g.rho0 = p->rho0;
+    g.p_a = p->p_a;
+    g.wavelength = p->wavelength;
+    g.antinode = p->antinode;
+    for (int a = 0; a < 3; ++a) g.center[a] = a < g.dim ? p->center[a] : 0.0;
+    g.radius = p->radius;
+    g.interface_d = p->interface_d;
+    g.surface_radius = p->surface_radius;
+    g.band_half = 20.0 * p->interface_d;
+    g.n_surface = p->n_surface;
+    g.stencil = g.dim == 3 ? 27 : 9;
+    return g;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Carve the workspace; with base == nullptr only the size is computed.
+size_t layout(const Geometry &g, bool f64, char *base, Buffers *b) {
+    const size_t T = f64 ? 8 : 4;
+    const size_t nc = (size_t)g.ncell, N = (size_t)g.n_surface, S = (size_t)g.stencil;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        void *ptr = base ? base + off : nullptr;
+        off += align256(bytes ? bytes : 1);
+        return ptr;
+    };
+    Buffers t{};
+    t.pop[0] = take(g.q * nc * T);
+    t.pop[1] = take(g.q * nc * T);
+    t.cls = (uint8_t *)take(nc);
+    t.c2 = take(nc * T);
+    t.pts = (double *)take(N * 7 * sizeof(double));
+    t.st_xyz = (int4 *)take(N * S * sizeof(int4));
+    t.st_w = take(N * S * 2 * T);
+    t.nrm = take(N * 4 * T);
+    t.acc = take(N * 5 * T);
+    t.acc64 = (double *)take(N * 5 * sizeof(double));
+    t.force = (double *)take(4 * sizeof(double));
+    t.err = (int *)take(sizeof(int));
+    t.stage_cells = g.ncell < kStageCells ? g.ncell : kStageCells;
+    t.stage = (double *)take((size_t)t.stage_cells * (1 + g.dim) * sizeof(double));
+    if (b) *b = t;
+    return off;
+}
+
+void destroy_graphs(wlb_handle *h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->graph_free[i]) cudaGraphExecDestroy(h->graph_free[i]);
+        if (h->graph_sampled[i]) cudaGraphExecDestroy(h->graph_sampled[i]);
+        h->graph_free[i] = h->graph_sampled[i] = nullptr;
+    }
+}
+
+// Issue one period of steps starting from buffer `start` on stream s.
+cudaError_t issue_period(wlb_handle *h, int start, bool sampled, cudaStream_t s) {
+    int cur = start;
+    for (long long t = 0; t < h->period; ++t) {
+        cudaError_t e;
+        if (sampled) {
+            e = wlb::launch_sample(h->g, h->b, h->f64, cur, s);
+            if (e != cudaSuccess) return e;
+        }
+        e = wlb::launch_update(h->g, h->b, h->f64, cur, s, nullptr);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    if (sampled) return wlb::launch_fold(h->g, h->b, h->f64, s);
+    return cudaSuccess;
+}
+
+wlb_status period_graph(wlb_handle *h, int start, bool sampled, cudaGraphExec_t *out) {
+    if (*out) return WLB_OK;
+    WLB_CUDA(h, cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = issue_period(h, start, sampled, h->capture);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->capture, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(h, WLB_ERR_CUDA, "capture period", e != cudaSuccess ? e : e2);
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return fail(h, WLB_ERR_CUDA, "instantiate period graph", e);
+    }
+    return WLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *wlb_status_str(wlb_status s) {
+    switch (s) {
+        case WLB_OK: return "ok";
+        case WLB_ERR_ARG: return "invalid argument";
+        case WLB_ERR_UNSTABLE: return "non-finite time averages (unstable run)";
+        case WLB_ERR_CUDA: return "CUDA error";
+        case WLB_ERR_OOM: return "out of memory or workspace too small";
+        case WLB_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char *wlb_last_error(const wlb_handle *h) { return h ? h->err : ""; }
+
+wlb_status wlb_validate(const wlb_params *p) {
+    if (!p) return WLB_ERR_ARG;
+    if (p->lattice != WLB_D2Q5 && p->lattice != WLB_D3Q7) return WLB_ERR_ARG;
+    if (p->precision != WLB_POP_F32 && p->precision != WLB_POP_F64) return WLB_ERR_ARG;
+    const int D = dim_of(p);
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return WLB_ERR_ARG;
+    if (D == 2 && p->nz != 1) return WLB_ERR_ARG;
+    if ((long long)p->nx * p->ny * p->nz > (1LL << 40)) return WLB_ERR_ARG;
+    if (p->wave_axis < 0 || p->wave_axis >= D) return WLB_ERR_ARG;
+    if (!(p->c0 > 0) || !(p->cp > 0) || !(p->rho0 > 0)) return WLB_ERR_ARG;
+    if (!(D * p->c0 * p->c0 < 1.0) || !(D * p->cp * p->cp < 1.0)) return WLB_ERR_ARG;
+    if (!std::isfinite(p->p_a) || !std::isfinite(p->antinode)) return WLB_ERR_ARG;
+    if (!(p->wavelength > 0) || !whole(p->wavelength / p->c0)) return WLB_ERR_ARG;
+    const int n[3] = {p->nx, p->ny, p->nz};
+    if (!whole(n[p->wave_axis] / p->wavelength)) return WLB_ERR_ARG;
+    if (!(p->radius > 0) || !(p->interface_d > 0) || !(p->surface_radius > 0)) return WLB_ERR_ARG;
+    if (p->n_surface < 0 || p->n_periods < 1) return WLB_ERR_ARG;
+    if (p->n_avg_periods < 0 || p->n_avg_periods > p->n_periods) return WLB_ERR_ARG;
+    // Object, interface band and interpolation stencil inside half the box.
+    const double band_r = std::sqrt(p->radius * p->radius + 20.0 * p->interface_d);
+    const double reach = std::fmax(band_r, p->surface_radius + 1.5) + 1.0;
+    for (int a = 0; a < D; ++a) {
+        if (!std::isfinite(p->center[a])) return WLB_ERR_ARG;
+        if (2.0 * reach > n[a]) return WLB_ERR_ARG;
+    }
+    const double T = p->wavelength / p->c0;
+    if ((double)p->n_periods * T > 9.0e15) return WLB_ERR_ARG;
+    return WLB_OK;
+}
+
+wlb_status wlb_workspace_bytes(const wlb_params *p, size_t *bytes) {
+    if (!bytes) return WLB_ERR_ARG;
+    wlb_status s = wlb_validate(p);
+    if (s != WLB_OK) return s;
+    *bytes = layout(make_geometry(p), p->precision == WLB_POP_F64, nullptr, nullptr);
+    return WLB_OK;
+}
+
+wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t workspace_bytes, void *stream,
+                      wlb_handle **out) {
+    if (!out) return WLB_ERR_ARG;
+    wlb_status s = wlb_validate(p);
+    if (s != WLB_OK) return s;
+    if (device_workspace && ((uintptr_t)device_workspace & 255u)) return WLB_ERR_ARG;
+    wlb_handle *h = new (std::nothrow) wlb_handle();
+    if (!h) return WLB_ERR_OOM;
+    h->p = *p;
+    h->g = make_geometry(p);
+    h->f64 = p->precision == WLB_POP_F64;
+    h->stream = (cudaStream_t)stream;
+    h->period = (long long)std::nearbyint(p->wavelength / p->c0);
+    h->n_steps = h->period * p->n_periods;
+    h->n_window = h->period * p->n_avg_periods;
+    h->vector_path = wlb::update_is_vectorised(h->g, h->f64);
+    const size_t need = layout(h->g, h->f64, nullptr, nullptr);
+    char *base = (char *)device_workspace;
+    if (base && workspace_bytes < need) {  // checked before any CUDA call
+        delete h;
+        return WLB_ERR_OOM;
+    }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return WLB_ERR_CUDA;
+    }
+    if (!base) {
+        e = cudaMalloc(&h->owned, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return WLB_ERR_OOM;
+        }
+        base = (char *)h->owned;
+    }
+    layout(h->g, h->f64, base, &h->b);
+    e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->host_out, 8 * sizeof(double), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        wlb_destroy(h);
+        return WLB_ERR_CUDA;
+    }
+    *out = h;
+    return WLB_OK;
+}
+
+wlb_status wlb_init(wlb_handle *h) {
+    if (!h) return WLB_ERR_ARG;
+    DeviceGuard dg(h->device);
+    WLB_CUDA(h, wlb::launch_setup(h->g, h->b, h->f64, h->stream), "setup kernels");
+    h->src = 0;
+    h->steps_done = h->samples_done = h->samples_in_period = 0;
+    h->initialised = true;
+    return WLB_OK;
+}
+
+wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
+    if (!h || n < 0) return WLB_ERR_ARG;
+    if (!h->initialised) return fail(h, WLB_ERR_STATE, "wlb_step before wlb_init");
+    DeviceGuard dg(h->device);
+    const bool sampled = sample != 0 && h->g.n_surface > 0;
+    while (n > 0) {
+        if (n >= h->period && (!sampled || h->samples_in_period == 0)) {
+            cudaGraphExec_t *slot = sampled ? &h->graph_sampled[h->src] : &h->graph_free[h->src];
+            wlb_status st = period_graph(h, h->src, sampled, slot);
+            if (st != WLB_OK) return st;
+            WLB_CUDA(h, cudaGraphLaunch(*slot, h->stream), "graph launch");
+            if (h->period & 1) h->src ^= 1;
+            h->steps_done += h->period;
+            if (sampled) h->samples_done += h->period;
+            n -= h->period;
+            continue;
+        }
+        if (sampled) WLB_CUDA(h, wlb::launch_sample(h->g, h->b, h->f64, h->src, h->stream), "sample kernel");
+        WLB_CUDA(h, wlb::launch_update(h->g, h->b, h->f64, h->src, h->stream, nullptr), "update kernel");
+        h->src ^= 1;
+        h->steps_done += 1;
+        if (sampled) {
+            h->samples_done += 1;
+            if (++h->samples_in_period == h->period) {
+                WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->f64, h->stream), "fold kernel");
+                h->samples_in_period = 0;
+            }
+        }
+        n -= 1;
+    }
+    return WLB_OK;
+}
+
+wlb_status wlb_force(wlb_handle *h, double force_out[3]) {
+    if (!h || !force_out) return WLB_ERR_ARG;
+    if (!h->initialised) return fail(h, WLB_ERR_STATE, "wlb_force before wlb_init");
+    DeviceGuard dg(h->device);
+    if (h->samples_done == 0 || h->g.n_surface == 0) {
+        force_out[0] = force_out[1] = force_out[2] = 0.0;
+        WLB_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+        return WLB_OK;
+    }
+    if (h->samples_in_period > 0) {
+        WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->f64, h->stream), "fold kernel");
+        h->samples_in_period = 0;
+    }
+    WLB_CUDA(h, wlb::launch_force(h->g, h->b, (double)h->samples_done, h->stream), "force kernel");
+    WLB_CUDA(h, cudaMemcpyAsync(h->host_out, h->b.force, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+             "force copy");
+    WLB_CUDA(h, cudaMemcpyAsync(h->host_out + 4, h->b.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+             "flag copy");
+    WLB_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+    int flag;
+    memcpy(&flag, h->host_out + 4, sizeof(int));
+    for (int i = 0; i < 3; ++i) force_out[i] = h->host_out[i];
+    if (flag) return fail(h, WLB_ERR_UNSTABLE, "non-finite accumulators");
+    return WLB_OK;
+}
+
+wlb_status wlb_run(wlb_handle *h, double force_out[3]) {
+    if (!h || !force_out) return WLB_ERR_ARG;
+    wlb_status s = wlb_init(h);
+    if (s == WLB_OK) s = wlb_step(h, h->n_steps - h->n_window, 0);
+    if (s == WLB_OK) s = wlb_step(h, h->n_window, 1);
+    if (s == WLB_OK) s = wlb_force(h, force_out);
+    return s;
+}
+
+wlb_status wlb_fields(wlb_handle *h, double *p1_out, double *u1_out) {
+    if (!h) return WLB_ERR_ARG;
+    if (!h->initialised) return fail(h, WLB_ERR_STATE, "wlb_fields before wlb_init");
+    DeviceGuard dg(h->device);
+    const long long nc = h->g.ncell, chunk = h->b.stage_cells;
+    for (long long first = 0; first < nc; first += chunk) {
+        const long long count = nc - first < chunk ? nc - first : chunk;
+        WLB_CUDA(h, wlb::launch_fields(h->g, h->b, h->f64, h->src, first, count, h->stream), "fields kernel");
+        if (p1_out)
+            WLB_CUDA(h, cudaMemcpyAsync(p1_out + first, h->b.stage, count * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->stream), "p1 copy");
+        if (u1_out)
+            for (int a = 0; a < h->g.dim; ++a)
+                WLB_CUDA(h, cudaMemcpyAsync(u1_out + (long long)a * nc + first, h->b.stage + (1 + a) * count,
+                                            count * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                         "u1 copy");
+        // the next chunk overwrites the staging buffer
+        WLB_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+    }
+    return WLB_OK;
+}
+
+wlb_status wlb_surface(wlb_handle *h, double *pts_out) {
+    if (!h || (!pts_out && h->g.n_surface > 0)) return WLB_ERR_ARG;
+    if (!h->initialised) return fail(h, WLB_ERR_STATE, "wlb_surface before wlb_init");
+    DeviceGuard dg(h->device);
+    if (h->g.n_surface > 0)
+        WLB_CUDA(h, cudaMemcpyAsync(pts_out, h->b.pts, (size_t)h->g.n_surface * 7 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream), "points copy");
+    WLB_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return WLB_OK;
+}
+
+wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out) {
+    if (!h || !mask_out) return WLB_ERR_ARG;
+    if (!h->initialised) return fail(h, WLB_ERR_STATE, "wlb_mask before wlb_init");
+    DeviceGuard dg(h->device);
+    WLB_CUDA(h, cudaMemcpyAsync(mask_out, h->b.cls, (size_t)h->g.ncell, cudaMemcpyDeviceToHost, h->stream),
+             "mask copy");
+    WLB_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return WLB_OK;
+}
+
+wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out) {
+    if (!h || !out) return WLB_ERR_ARG;
+    out->dim = h->g.dim;
+    out->q = h->g.q;
+    out->cells = h->g.ncell;
+    out->period = h->period;
+    out->n_steps = h->n_steps;
+    out->n_window = h->n_window;
+    out->steps_done = h->steps_done;
+    out->samples_done = h->samples_done;
+    out->bytes_per_update = 2.0 * h->g.q * (h->f64 ? 8.0 : 4.0) + 1.0;
+    out->vector_path = h->vector_path ? 1 : 0;
+    return WLB_OK;
+}
+
+wlb_status wlb_destroy(wlb_handle *h) {
+    if (!h) return WLB_ERR_ARG;
+    DeviceGuard dg(h->device);
+    destroy_graphs(h);
+    if (h->capture) cudaStreamDestroy(h->capture);
+    if (h->host_out) cudaFreeHost(h->host_out);
+    if (h->owned) cudaFree(h->owned);
+    delete h;
+    return WLB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wlb {
+
+// Cell classes (the byte field read by the update kernel).
+enum : uint8_t { CELL_FLUID = 0, CELL_OBJECT = 1, CELL_BAND = 2 };
+
+// Problem description as the kernels see it (passed by value).
+struct Geometry {
+    int dim, q;            // 2 or 3; 5 or 7
+    int n[3];              // nx, ny, nz
+    long long ncell;       // nx*ny*nz
+    int wave_axis;
+    double c0, cp, rho0;
+    double p_a, wavelength, antinode;
+    double center[3];
+    double radius, interface_d, surface_radius;
+    double band_half;      // class threshold on |x-r0|^2 - R^2 (20 d)
+    int n_surface;
+    int stencil;           // 3^dim
+};
+
+// Device buffers carved from one workspace.
+struct Buffers {
+    void *pop[2];          // populations, q * ncell of T each
+    uint8_t *cls;          // ncell
+    void *c2;              // ncell of T: sound speed squared (read for band cells)
+    double *pts;           // n_surface * 7
+    int4 *st_xyz;          // n_surface * stencil: wrapped cell coordinates
+    void *st_w;            // n_surface * stencil * 2 of T: (delta c^2, delta / rho0)
+    void *nrm;             // n_surface * 4 of T: normal (x, y, z, 0)
+    void *acc;             // n_surface * 5 of T: running sums within a period
+    double *acc64;         // n_surface * 5: folded sums
+    double *force;         // 4 doubles
+    int *err;              // 1 int: non-finite accumulator seen
+    double *stage;         // stage_cells * (1 + dim): field read-back staging
+    long long stage_cells;
+};
+
+// Launchers (each TU owns its kernels).  All return cudaGetLastError().
+cudaError_t launch_setup(const Geometry &g, const Buffers &b, bool f64, cudaStream_t s);
+cudaError_t launch_update(const Geometry &g, const Buffers &b, bool f64, int src, cudaStream_t s,
+                          bool *vector_path);
+cudaError_t launch_sample(const Geometry &g, const Buffers &b, bool f64, int src, cudaStream_t s);
+cudaError_t launch_fold(const Geometry &g, const Buffers &b, bool f64, cudaStream_t s);
+cudaError_t launch_force(const Geometry &g, const Buffers &b, double n_window, cudaStream_t s);
+cudaError_t launch_fields(const Geometry &g, const Buffers &b, bool f64, int src,
+                          long long first_cell, long long count, cudaStream_t s);
+bool update_is_vectorised(const Geometry &g, bool f64);
+
+}  // namespace wlb

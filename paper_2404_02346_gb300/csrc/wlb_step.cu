@@ -1,0 +1,404 @@
+// Per-step kernels of the wave lattice Boltzmann force computation.
+//
+//   update   fused advection + BGK collision with tau = 1/2 (Sec. V, Eqs. 62-64,
+//            71), pull form: the populations that reach cell x are read from
+//            x - v_i and the post-collision values are written at x.
+//   sample   kernel interpolation of p1 and u1 onto the surface elements
+//            (Sec. VI, Eqs. 80-82) and running sums of p1^2, u1.u1, (n.u1) u1.
+//   fold     once per period: running sums -> FP64 totals.
+//   force    King's surface integral, Eq. (14), in FP64.
+//   fields   p1 = c^2 rho1 and u1 = J1 / rho0 (Eq. 62) for read-back.
+//
+// With tau = 1/2 the collision f* = 2 f^eq - f becomes, with the equilibrium of
+// Eq. (71) (w_i / c_s^2 = 1/2 for both D2Q5 and D3Q7),
+//     f*_0  = 2 rho1 (1 - D c^2) - f_0,
+//     f*_+a = c^2 rho1 + J_a - f_+a = c^2 rho1 - f_-a,
+//     f*_-a = c^2 rho1 - J_a - f_-a = c^2 rho1 - f_+a.
+#include "wlb_internal.cuh"
+
+namespace wlb {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// 16-byte vector access with streaming cache hints: every population is read
+// once and written once per step.
+__device__ __forceinline__ void load16(const float *p, float (&v)[4]) {
+    float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load16(const double *p, double (&v)[2]) {
+    double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
+    v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void store16(float *p, const float (&v)[4]) {
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+__device__ __forceinline__ void store16(double *p, const double (&v)[2]) {
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+}
+template <int W>
+__device__ __forceinline__ uint32_t load_classes(const uint8_t *p) {
+    if constexpr (W == 4) return *reinterpret_cast<const uint32_t *>(p);
+    else return *reinterpret_cast<const uint16_t *>(p);
+}
+
+// Row-vectorised update.  One warp owns one lattice row (fixed y, z) of
+// nx = 32 * W * CH cells; lane L holds cells (c*32 + L)*W .. +W-1 of chunk c.
+// Every population row is read with aligned 16-byte loads: the +-y and +-z
+// neighbours are whole rows, and the +-x shift (including the periodic wrap at
+// the row ends) is done with warp shuffles, so no element is loaded twice.
+template <typename T, int D, int CH>
+__global__ void __launch_bounds__(256) update_rows(const T *__restrict__ src, T *__restrict__ dst,
+                                                   const uint8_t *__restrict__ cls,
+                                                   const T *__restrict__ c2f, int nx, int ny, int nz,
+                                                   long long ncell, T c0sq, T cpsq) {
+    constexpr int W = 16 / sizeof(T);
+    constexpr int Q = 2 * D + 1;
+    const int lane = threadIdx.x & 31;
+    const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= (long long)ny * nz) return;  // uniform per warp
+    const int y = (int)(row % ny);
+    const int z = (int)(row / ny);
+    const int ym = y == 0 ? ny - 1 : y - 1;
+    const int yp = y == ny - 1 ? 0 : y + 1;
+    const long long r0 = row * nx;
+    const long long rym = ((long long)z * ny + ym) * nx;
+    const long long ryp = ((long long)z * ny + yp) * nx;
+    long long rzm = 0, rzp = 0;
+    if (D == 3) {
+        const int zm = z == 0 ? nz - 1 : z - 1;
+        const int zp = z == nz - 1 ? 0 : z + 1;
+        rzm = ((long long)zm * ny + y) * nx;
+        rzp = ((long long)zp * ny + y) * nx;
+    }
+
+    T f[Q][CH][W];
+    uint32_t cl[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int x0 = (c * 32 + lane) * W;
+        load16(src + r0 + x0, f[0][c]);
+        load16(src + ncell + r0 + x0, f[1][c]);
+        load16(src + 2 * ncell + r0 + x0, f[2][c]);
+        load16(src + 3 * ncell + rym + x0, f[3][c]);
+        load16(src + 4 * ncell + ryp + x0, f[4][c]);
+        if (D == 3) {
+            load16(src + 5 * ncell + rzm + x0, f[5][c]);
+            load16(src + 6 * ncell + rzp + x0, f[6][c]);
+        }
+        cl[c] = load_classes<W>(cls + r0 + x0);
+    }
+
+    // The +x population arriving at x left x-1; the -x one left x+1.
+    T up[CH], dn[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        up[c] = __shfl_sync(kFull, f[1][c][W - 1], (lane + 31) & 31);
+        dn[c] = __shfl_sync(kFull, f[2][c][0], (lane + 1) & 31);
+    }
+
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int x0 = (c * 32 + lane) * W;
+        T fpx[W], fmx[W];
+        fpx[0] = lane == 0 ? up[(c + CH - 1) % CH] : up[c];
+#pragma unroll
+        for (int e = 1; e < W; ++e) fpx[e] = f[1][c][e - 1];
+#pragma unroll
+        for (int e = 0; e < W - 1; ++e) fmx[e] = f[2][c][e + 1];
+        fmx[W - 1] = lane == 31 ? dn[(c + 1) % CH] : dn[c];
+
+        T o[Q][W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            const uint32_t k = (cl[c] >> (8 * e)) & 0xffu;
+            const T c2 = k == CELL_FLUID ? c0sq : (k == CELL_OBJECT ? cpsq : c2f[r0 + x0 + e]);
+            T rho = f[0][c][e] + fpx[e] + fmx[e] + f[3][c][e] + f[4][c][e];
+            if (D == 3) rho += f[5][c][e] + f[6][c][e];
+            const T eq = c2 * rho;
+            o[0][e] = T(2) * (rho - T(D) * eq) - f[0][c][e];
+            o[1][e] = eq - fmx[e];
+            o[2][e] = eq - fpx[e];
+            o[3][e] = eq - f[4][c][e];
+            o[4][e] = eq - f[3][c][e];
+            if (D == 3) {
+                o[5][e] = eq - f[6][c][e];
+                o[6][e] = eq - f[5][c][e];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) store16(dst + i * ncell + r0 + x0, o[i]);
+    }
+}
+
+// Any lattice shape: one thread per cell, scalar accesses.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) update_cells(const T *__restrict__ src, T *__restrict__ dst,
+                                                    const uint8_t *__restrict__ cls,
+                                                    const T *__restrict__ c2f, int nx, int ny, int nz,
+                                                    long long ncell, T c0sq, T cpsq) {
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= ncell) return;
+    const int x = (int)(id % nx);
+    const long long r = id / nx;
+    const int y = (int)(r % ny);
+    const int z = (int)(r / ny);
+    const long long row = id - x;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const T f0 = src[id];
+    const T fpx = src[ncell + row + xm];
+    const T fmx = src[2 * ncell + row + xp];
+    const T fpy = src[3 * ncell + ((long long)z * ny + ym) * nx + x];
+    const T fmy = src[4 * ncell + ((long long)z * ny + yp) * nx + x];
+    T fpz = 0, fmz = 0;
+    if (D == 3) {
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        fpz = src[5 * ncell + ((long long)zm * ny + y) * nx + x];
+        fmz = src[6 * ncell + ((long long)zp * ny + y) * nx + x];
+    }
+    const uint8_t k = cls[id];
+    const T c2 = k == CELL_FLUID ? c0sq : (k == CELL_OBJECT ? cpsq : c2f[id]);
+    T rho = f0 + fpx + fmx + fpy + fmy;
+    if (D == 3) rho += fpz + fmz;
+    const T eq = c2 * rho;
+    dst[id] = T(2) * (rho - T(D) * eq) - f0;
+    dst[ncell + id] = eq - fmx;
+    dst[2 * ncell + id] = eq - fpx;
+    dst[3 * ncell + id] = eq - fmy;
+    dst[4 * ncell + id] = eq - fpy;
+    if (D == 3) {
+        dst[5 * ncell + id] = eq - fmz;
+        dst[6 * ncell + id] = eq - fpz;
+    }
+}
+
+// rho1 and J1 at cell (x, y, z) at the current time: the pull-sum of the stored
+// post-collision populations (Eq. 62 applied after the advection of Eq. 64).
+template <typename T>
+__device__ __forceinline__ void pulled_moments(const Geometry &g, const T *__restrict__ src, int x,
+                                               int y, int z, T &rho, T (&J)[3]) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long nc = g.ncell;
+    const long long id = ((long long)z * ny + y) * nx + x;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const T f0 = src[id];
+    const T fpx = src[nc + id - x + xm];
+    const T fmx = src[2 * nc + id - x + xp];
+    const T fpy = src[3 * nc + ((long long)z * ny + ym) * nx + x];
+    const T fmy = src[4 * nc + ((long long)z * ny + yp) * nx + x];
+    rho = f0 + fpx + fmx + fpy + fmy;
+    J[0] = fpx - fmx;
+    J[1] = fpy - fmy;
+    J[2] = T(0);
+    if (g.dim == 3) {
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        const T fpz = src[5 * nc + ((long long)zm * ny + y) * nx + x];
+        const T fmz = src[6 * nc + ((long long)zp * ny + y) * nx + x];
+        rho += fpz + fmz;
+        J[2] = fpz - fmz;
+    }
+}
+
+// One warp per surface element; lane l < 3^dim handles stencil cell l.
+// P = sum_l delta_l c_l^2 rho1_l and U = sum_l delta_l J1_l / rho0 (Eqs. 80-81),
+// then acc += (P^2, U.U, U_x (U.n), U_y (U.n), U_z (U.n)).
+template <typename T>
+__global__ void __launch_bounds__(256) sample_points(Geometry g, const T *__restrict__ src,
+                                                     const int4 *__restrict__ st_xyz,
+                                                     const T *__restrict__ st_w,
+                                                     const T *__restrict__ nrm, T *__restrict__ acc) {
+    const int lane = threadIdx.x & 31;
+    const int k = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (k >= g.n_surface) return;  // uniform per warp
+    T p = T(0), u[3] = {T(0), T(0), T(0)};
+    if (lane < g.stencil) {
+        const long long o = (long long)k * g.stencil + lane;
+        const int4 c = st_xyz[o];
+        T rho, J[3];
+        pulled_moments(g, src, c.x, c.y, c.z, rho, J);
+        const T wp = st_w[2 * o], wu = st_w[2 * o + 1];
+        p = wp * rho;
+        u[0] = wu * J[0];
+        u[1] = wu * J[1];
+        u[2] = wu * J[2];
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        p += __shfl_xor_sync(kFull, p, m);
+        u[0] += __shfl_xor_sync(kFull, u[0], m);
+        u[1] += __shfl_xor_sync(kFull, u[1], m);
+        u[2] += __shfl_xor_sync(kFull, u[2], m);
+    }
+    if (lane == 0) {
+        const T nx = nrm[4 * k], ny = nrm[4 * k + 1], nz = nrm[4 * k + 2];
+        const T un = u[0] * nx + u[1] * ny + u[2] * nz;
+        T *a = acc + 5 * (long long)k;
+        a[0] += p * p;
+        a[1] += u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        a[2] += u[0] * un;
+        a[3] += u[1] * un;
+        a[4] += u[2] * un;
+    }
+}
+
+template <typename T>
+__global__ void fold_sums(int n, T *__restrict__ acc, double *__restrict__ acc64, int *__restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = acc64[i] + (double)acc[i];
+    acc64[i] = v;
+    acc[i] = T(0);
+    if (!isfinite(v)) atomicExch(err, 1);
+}
+
+// Eq. (14) on the surface elements; one block, fixed reduction order.
+__global__ void __launch_bounds__(256) surface_force(Geometry g, const double *__restrict__ pts,
+                                                     const double *__restrict__ acc64, double inv_nw,
+                                                     double *__restrict__ force, int *__restrict__ err) {
+    __shared__ double red[3][256];
+    const int t = threadIdx.x;
+    double F[3] = {0.0, 0.0, 0.0};
+    const double rho0 = g.rho0;
+    const double inv_2rc2 = 1.0 / (2.0 * rho0 * g.c0 * g.c0);
+    for (int k = t; k < g.n_surface; k += blockDim.x) {
+        const double *row = pts + 7 * (long long)k;
+        const double *a = acc64 + 5 * (long long)k;
+        const double iso = a[0] * inv_nw * inv_2rc2 - 0.5 * rho0 * (a[1] * inv_nw);
+        for (int i = 0; i < 3; ++i) F[i] -= row[6] * (iso * row[3 + i] + rho0 * (a[2 + i] * inv_nw));
+    }
+    for (int i = 0; i < 3; ++i) red[i][t] = F[i];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s)
+            for (int i = 0; i < 3; ++i) red[i][t] += red[i][t + s];
+        __syncthreads();
+    }
+    if (t == 0) {
+        for (int i = 0; i < 3; ++i) {
+            const double v = i < g.dim ? red[i][0] : 0.0;
+            force[i] = v;
+            if (!isfinite(v)) atomicExch(err, 1);
+        }
+        force[3] = 0.0;
+    }
+}
+
+template <typename T>
+__global__ void read_fields(Geometry g, const T *__restrict__ src, const uint8_t *__restrict__ cls,
+                            const T *__restrict__ c2f, long long first, long long count,
+                            double *__restrict__ stage) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    const long long id = first + j;
+    const int x = (int)(id % g.n[0]);
+    const long long r = id / g.n[0];
+    const int y = (int)(r % g.n[1]);
+    const int z = (int)(r / g.n[1]);
+    T rho, J[3];
+    pulled_moments(g, src, x, y, z, rho, J);
+    const uint8_t k = cls[id];
+    const double c2 = k == CELL_FLUID ? (double)(T)(g.c0 * g.c0)
+                                      : (k == CELL_OBJECT ? (double)(T)(g.cp * g.cp) : (double)c2f[id]);
+    stage[j] = c2 * (double)rho;
+    for (int a = 0; a < g.dim; ++a) stage[(long long)(1 + a) * count + j] = (double)J[a] / g.rho0;
+}
+
+template <typename T, int D, int CH>
+cudaError_t run_rows(const Geometry &g, const Buffers &b, int src, cudaStream_t s) {
+    const long long rows = (long long)g.n[1] * g.n[2];
+    const long long blocks = (rows * 32 + 255) / 256;
+    update_rows<T, D, CH><<<(unsigned)blocks, 256, 0, s>>>(
+        (const T *)b.pop[src], (T *)b.pop[src ^ 1], b.cls, (const T *)b.c2, g.n[0], g.n[1], g.n[2],
+        g.ncell, (T)(g.c0 * g.c0), (T)(g.cp * g.cp));
+    return cudaGetLastError();
+}
+
+template <typename T, int D>
+cudaError_t run_update(const Geometry &g, const Buffers &b, int src, cudaStream_t s, bool *vec) {
+    constexpr int W = 16 / sizeof(T);
+    const int nx = g.n[0];
+    if (nx % (32 * W) == 0) {
+        const int ch = nx / (32 * W);
+        *vec = true;
+        switch (ch) {
+            case 1: return run_rows<T, D, 1>(g, b, src, s);
+            case 2: return run_rows<T, D, 2>(g, b, src, s);
+            case 3: return run_rows<T, D, 3>(g, b, src, s);
+            case 4: return run_rows<T, D, 4>(g, b, src, s);
+            default: break;
+        }
+    }
+    *vec = false;
+    const long long blocks = (g.ncell + 255) / 256;
+    update_cells<T, D><<<(unsigned)blocks, 256, 0, s>>>(
+        (const T *)b.pop[src], (T *)b.pop[src ^ 1], b.cls, (const T *)b.c2, g.n[0], g.n[1], g.n[2],
+        g.ncell, (T)(g.c0 * g.c0), (T)(g.cp * g.cp));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool update_is_vectorised(const Geometry &g, bool f64) {
+    const int W = f64 ? 2 : 4;
+    if (g.n[0] % (32 * W) != 0) return false;
+    const int ch = g.n[0] / (32 * W);
+    return ch >= 1 && ch <= 4;
+}
+
+cudaError_t launch_update(const Geometry &g, const Buffers &b, bool f64, int src, cudaStream_t s,
+                          bool *vector_path) {
+    bool vec = false;
+    cudaError_t e;
+    if (f64)
+        e = g.dim == 3 ? run_update<double, 3>(g, b, src, s, &vec) : run_update<double, 2>(g, b, src, s, &vec);
+    else
+        e = g.dim == 3 ? run_update<float, 3>(g, b, src, s, &vec) : run_update<float, 2>(g, b, src, s, &vec);
+    if (vector_path) *vector_path = vec;
+    return e;
+}
+
+cudaError_t launch_sample(const Geometry &g, const Buffers &b, bool f64, int src, cudaStream_t s) {
+    if (g.n_surface == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((g.n_surface + 7) / 8);
+    if (f64)
+        sample_points<double><<<blocks, 256, 0, s>>>(g, (const double *)b.pop[src], b.st_xyz,
+                                                     (const double *)b.st_w, (const double *)b.nrm,
+                                                     (double *)b.acc);
+    else
+        sample_points<float><<<blocks, 256, 0, s>>>(g, (const float *)b.pop[src], b.st_xyz,
+                                                    (const float *)b.st_w, (const float *)b.nrm,
+                                                    (float *)b.acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(const Geometry &g, const Buffers &b, bool f64, cudaStream_t s) {
+    if (g.n_surface == 0) return cudaSuccess;
+    const int n = 5 * g.n_surface;
+    if (f64)
+        fold_sums<double><<<(n + 255) / 256, 256, 0, s>>>(n, (double *)b.acc, b.acc64, b.err);
+    else
+        fold_sums<float><<<(n + 255) / 256, 256, 0, s>>>(n, (float *)b.acc, b.acc64, b.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force(const Geometry &g, const Buffers &b, double n_window, cudaStream_t s) {
+    surface_force<<<1, 256, 0, s>>>(g, b.pts, b.acc64, 1.0 / n_window, b.force, b.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const Geometry &g, const Buffers &b, bool f64, int src, long long first,
+                          long long count, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((count + 255) / 256);
+    if (f64)
+        read_fields<double><<<blocks, 256, 0, s>>>(g, (const double *)b.pop[src], b.cls,
+                                                   (const double *)b.c2, first, count, b.stage);
+    else
+        read_fields<float><<<blocks, 256, 0, s>>>(g, (const float *)b.pop[src], b.cls,
+                                                  (const float *)b.c2, first, count, b.stage);
+    return cudaGetLastError();
+}
+
+}  // namespace wlb

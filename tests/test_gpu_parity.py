@@ -1,0 +1,221 @@
+"""GPU path vs the FP64 oracle, through the C ABI (paper_2404_02346_gb300).
+
+Bars (spec tolerances): cell classes and surface points bit-exact;
+p1 (and u1) within 1e-4 p_a max-abs after the run; force within 1e-3 relative.
+The FP64-population path is held to far tighter bounds than these.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import theory
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wlb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2404_02346_gb300 import build as B
+    B.build()
+    import paper_2404_02346_gb300 as W
+    W.lib()
+    return W
+
+
+def _gpu_run(W, prob, fields=True, precision=None):
+    with W.Solver(prob, precision=precision) as s:
+        F = s.run()
+        out = {"force": F, "mask": s.mask(), "points": s.surface(), "info": s.info()}
+        if fields:
+            out["p1"], out["u1"] = s.fields()
+    return out
+
+
+def _compare(prob, g, o, p1_tol, force_rtol):
+    assert np.array_equal(g["mask"], oracle.mask(prob))
+    if prob["n_surface"]:
+        assert np.array_equal(g["points"], o["points"])  # bit-exact, same IEEE sequence
+    pa = prob["p_a"]
+    if "p1" in o:
+        assert np.abs(g["p1"] - o["p1"]).max() <= p1_tol * pa
+        assert np.abs(g["u1"] - o["u1"]).max() <= p1_tol * pa / prob["c0"]
+    Fo, Fg = o["force"], g["force"]
+    axis = prob["wave_axis"]
+    assert abs(Fg[axis] - Fo[axis]) <= force_rtol * abs(Fo[axis])
+    # lateral components: small both ways, compared on the scale of the axial force
+    assert np.all(np.abs(Fg - Fo) <= max(force_rtol, 1e-6) * abs(Fo[axis]) + 1e-30)
+
+
+def test_cylinder_2d_fp64_full_run(wlb):
+    """128 x 128 D2Q5 FP64, lambda = 64, R = 8 at lambda/8 with seeded jitter,
+    cp = 1.5 c0, 64 points, 20 periods averaged over the last 5 (5120 steps)."""
+    prob = workloads.cylinder_2d(seed=1)
+    o = oracle.run(prob, fields=True)
+    g = _gpu_run(wlb, prob)
+    assert g["info"].vector_path == 1
+    _compare(prob, g, o, p1_tol=1e-9, force_rtol=1e-9)
+
+
+def test_cylinder_2d_fp32_populations(wlb):
+    prob = workloads.cylinder_2d(seed=2)
+    o = oracle.run(prob, fields=True)
+    g = _gpu_run(wlb, prob, precision="f32")
+    _compare(prob, g, o, p1_tol=1e-4, force_rtol=1e-3)
+
+
+@pytest.mark.parametrize("shape,lam,R,N", [((128, 48, 64), 32.0, 6.0, 500),
+                                           ((256, 24, 32), 16.0, 3.0, 300),
+                                           ((40, 36, 32), 16.0, 4.0, 200)])
+def test_sphere_3d_fp32_full_protocol(wlb, shape, lam, R, N):
+    """D3Q7 FP32 over 30 periods averaged over the last 10, at sizes the oracle
+    finishes in seconds: nx = 128 and 256 take the row-vectorised kernel (one
+    and two 128-cell chunks per warp), nx = 40 the per-cell kernel."""
+    nx, ny, nz = shape
+    prob = workloads.problem(3, shape, 2, lam, R, (nx / 2 + 0.375, ny / 2 - 0.25, lam / 8 + 0.125),
+                             cp=0.25 / math.sqrt(0.35), n_surface=N, n_periods=30, n_avg_periods=10)
+    o = oracle.run(prob, fields=True)
+    g = _gpu_run(wlb, prob)
+    assert g["info"].vector_path == (1 if nx % 128 == 0 else 0)
+    _compare(prob, g, o, p1_tol=1e-4, force_rtol=1e-3)
+
+
+def test_sphere_256_full_size_short_run(wlb):
+    """The benchmark's 256^3 D3Q7 FP32 lattice and 2000 points in the launch
+    configuration it times, for a few steps the oracle can follow: classes and
+    points bit-exact, fields and the short-window force within tolerance."""
+    prob = workloads.sphere_3d(seed=1)
+    short = dict(prob, n_steps=8, n_window=4)
+    o = oracle.run(short, fields=True)
+    with wlb.Solver(prob) as s:
+        s.init()
+        s.step(4, sample=False)
+        s.step(4, sample=True)
+        F = s.force()
+        p1, u1 = s.fields()
+        g = {"force": F, "mask": s.mask(), "points": s.surface(), "p1": p1, "u1": u1}
+        assert s.info().vector_path == 1
+    _compare(short, g, o, p1_tol=1e-5, force_rtol=1e-4)
+
+
+def test_sphere_256_full_length_uniform_medium_closed_form(wlb):
+    """Full size and full length (256^3, 15360 steps, the benchmark's launch
+    configuration) with cp = c0: the field must stay the closed-form lattice mode
+    p1 = p_a cos(k s) cos(w t) that pins the oracle, within 1e-4 p_a."""
+    prob = dict(workloads.sphere_3d(seed=1))
+    prob["cp"] = prob["c0"]
+    with wlb.Solver(prob) as s:
+        s.run()
+        p1, _ = s.fields()
+        steps = s.info().steps_done
+    k = 2 * math.pi / prob["wavelength"]
+    w = theory.lattice_omega([0.0, 0.0, k], prob["c0"] ** 2)
+    z = np.arange(prob["n"][2]) - prob["antinode"]
+    want = prob["p_a"] * np.cos(k * z)[:, None, None] * math.cos(w * steps)
+    assert np.abs(p1 - want).max() <= 1e-4 * prob["p_a"]
+
+
+def test_sphere_256_full_length_pressure_scaling_is_exact(wlb):
+    """Full benchmark run at p_a and 2 p_a: every FP32 population doubles exactly,
+    so the force quadruples bit for bit (Tables II-III: exponent 2)."""
+    prob = workloads.sphere_3d(seed=1)
+    F1 = _gpu_run(wlb, prob, fields=False)["force"]
+    F2 = _gpu_run(wlb, dict(prob, p_a=2 * prob["p_a"]), fields=False)["force"]
+    assert np.array_equal(F2, 4 * F1)
+    gk = theory.gorkov_force_3d(prob["radius"], prob["p_a"], prob["wavelength"], prob["center"][2],
+                                prob["c0"], prob["cp"])
+    assert F1[2] > 0 and 0.3 < F1[2] / gk < 3  # same sign and order as Gor'kov at kR = 0.79
+    assert np.all(np.abs(F1[:2]) < 0.05 * abs(F1[2]))
+
+
+def test_node_symmetry_2d(wlb):
+    """Object at the pressure node: the lattice is mirror symmetric, F_s = 0."""
+    prob = workloads.problem(2, (64, 64), 1, 64.0, 6.0, (32.0, 16.0), cp=0.375, n_surface=64,
+                             n_periods=4, n_avg_periods=2, precision="f64")
+    g = _gpu_run(wlb, prob, fields=False)
+    off = workloads.problem(2, (64, 64), 1, 64.0, 6.0, (32.0, 8.0), cp=0.375, n_surface=64,
+                            n_periods=4, n_avg_periods=2, precision="f64")
+    ref = _gpu_run(wlb, off, fields=False)["force"][1]
+    assert abs(g["force"][1]) < 1e-9 * abs(ref)
+
+
+def test_edge_cases(wlb):
+    # odd period (T = 25): per-period graphs alternate between the two buffers
+    prob = workloads.problem(2, (40, 20), 1, 5.0, 1.5, (20.0, 10.0), cp=0.3, c0=0.2,
+                             n_surface=16, n_periods=5, n_avg_periods=2, precision="f64",
+                             interface_d=0.5)
+    assert prob["period"] == 25
+    o = oracle.run(prob, fields=True)
+    _compare(prob, _gpu_run(wlb, prob), o, p1_tol=1e-9, force_rtol=1e-9)
+    # tiny ragged lattice, sharp interface
+    tiny = workloads.problem(2, (9, 8), 1, 8.0, 1.0, (4.25, 4.0), cp=0.3, n_surface=8,
+                             n_periods=2, n_avg_periods=1, precision="f32", interface_d=0.25)
+    o = oracle.run(tiny, fields=True)
+    _compare(tiny, _gpu_run(wlb, tiny), o, p1_tol=1e-5, force_rtol=1e-3)
+    # no surface points / empty averaging window -> zero force, fields still parity
+    for kw in ({"n_surface": 0}, {"n_window": 0}):
+        p = dict(tiny, **kw)
+        g = _gpu_run(wlb, p)
+        assert np.array_equal(g["force"], np.zeros(3))
+        assert np.abs(g["p1"] - oracle.run(p, fields=True)["p1"]).max() <= 1e-5 * p["p_a"]
+
+
+def test_wave_along_x_and_stepwise_calls(wlb):
+    """Wave along x (the row axis of the update kernel), sampled steps split
+    across calls at non-period boundaries, against the oracle."""
+    prob = workloads.problem(3, (64, 24, 24), 0, 32.0, 3.0, (8.25, 12.0, 12.5), cp=0.45,
+                             n_surface=150, n_periods=3, n_avg_periods=2)
+    o = oracle.run(prob, fields=True)
+    with wlb.Solver(prob) as s:
+        s.init()
+        s.step(100, sample=False)
+        s.step(28, sample=False)
+        for n in (1, 37, 90, 128):
+            s.step(n, sample=True)
+        F = s.force()
+        p1, u1 = s.fields()
+        g = {"force": F, "mask": s.mask(), "points": s.surface(), "p1": p1, "u1": u1}
+    _compare(prob, g, o, p1_tol=1e-5, force_rtol=1e-4)
+
+
+def test_errors_are_reported_not_faulted(wlb):
+    import ctypes
+    L = wlb.lib()
+    prob = workloads.problem(2, (32, 32), 1, 32.0, 3.0, (16.0, 8.0), cp=0.3, n_surface=8,
+                             n_periods=2, n_avg_periods=1, precision="f32")
+    s = wlb.Solver(prob)
+    assert L.wlb_step(s._h, 1, 0) == wlb.WLB_ERR_STATE
+    F = (ctypes.c_double * 3)()
+    assert L.wlb_force(s._h, F) == wlb.WLB_ERR_STATE
+    s.close()
+    # overflowing amplitudes give non-finite running sums: reported, not faulted
+    big = dict(prob, p_a=1e30)
+    with wlb.Solver(big) as s2:
+        with pytest.raises(wlb.WlbError) as e:
+            s2.run()
+        assert e.value.status == wlb.WLB_ERR_UNSTABLE
+
+
+def test_non_default_stream_and_library_workspace(wlb):
+    import ctypes
+    import torch
+    prob = workloads.problem(2, (64, 32), 1, 32.0, 4.0, (32.0, 4.0), cp=0.375, n_surface=32,
+                             n_periods=2, n_avg_periods=1, precision="f64")
+    ref = oracle.run(prob)["force"]
+    st = torch.cuda.Stream()
+    with wlb.Solver(prob, stream=st) as s:
+        F = s.run()
+    assert abs(F[1] - ref[1]) <= 1e-9 * abs(ref[1])
+    # library-owned workspace (NULL) on the legacy default stream
+    L = wlb.lib()
+    p = wlb.params_from_problem(prob)
+    h = ctypes.c_void_p()
+    assert L.wlb_create(ctypes.byref(p), None, 0, None, ctypes.byref(h)) == wlb.WLB_OK
+    F2 = np.zeros(3)
+    assert L.wlb_run(h, F2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == wlb.WLB_OK
+    assert L.wlb_destroy(h) == wlb.WLB_OK
+    assert np.array_equal(F2, F)
