@@ -145,14 +145,14 @@ def test_node_symmetry_2d(wlb):
 
 def test_edge_cases(wlb):
     # odd period (T = 25): per-period graphs alternate between the two buffers
-    prob = workloads.problem(2, (40, 20), 1, 5.0, 1.5, (20.0, 10.0), cp=0.3, c0=0.2,
+    prob = workloads.problem(2, (40, 20), 1, 5.0, 1.5, (20.0, 10.625), cp=0.3, c0=0.2,
                              n_surface=16, n_periods=5, n_avg_periods=2, precision="f64",
                              interface_d=0.5)
     assert prob["period"] == 25
     o = oracle.run(prob, fields=True)
     _compare(prob, _gpu_run(wlb, prob), o, p1_tol=1e-9, force_rtol=1e-9)
     # tiny ragged lattice, sharp interface
-    tiny = workloads.problem(2, (9, 8), 1, 8.0, 1.0, (4.25, 4.0), cp=0.3, n_surface=8,
+    tiny = workloads.problem(2, (9, 8), 1, 8.0, 1.0, (4.25, 5.0), cp=0.3, n_surface=8,
                              n_periods=2, n_avg_periods=1, precision="f32", interface_d=0.25)
     o = oracle.run(tiny, fields=True)
     _compare(tiny, _gpu_run(wlb, tiny), o, p1_tol=1e-5, force_rtol=1e-3)
