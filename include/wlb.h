@@ -174,6 +174,40 @@ wlb_status wlb_surface(wlb_handle *h, double *pts_out);
  * of Eq. (79) is +-1 in double precision.  Synchronises. */
 wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out);
 
+/*
+ * Allocation-free averaging (the paper has no counterpart of this call).
+ *
+ * For callers that cannot allocate device memory when they need a force:
+ * code running while a CUDA graph is captured in global mode (an allocation
+ * would invalidate the capture), processes whose device memory belongs to a
+ * fixed pool under a hard budget, and latency-bound loops that must not wait
+ * on an allocator.  Starting from the handle's current state, advances
+ * n_steps >= 0 sampled steps exactly as wlb_step(h, n_steps, 1) does
+ * (interpolation, running sums folded to FP64 once per period, fused
+ * stream+collide) and then returns the time-averaged force over those
+ * n_steps, as wlb_force would for them, in force_out (3 host doubles; zeros
+ * when n_steps == 0 or n_surface == 0).  Synchronises the handle's stream.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine and
+ * instantiates no graph: kernels are launched directly, and the running
+ * sums, FP64 totals, force and error flag live in one file-scope device array
+ * of 640 KiB, sized for WLB_NOALLOC_MAX_SURFACE points, that every GPU
+ * loading the library holds until the process exits.  The handle's own
+ * accumulators and sample counters are left untouched.
+ *
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress, with that device current); make this first call
+ *     before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents; each
+ *     call clears what it accumulates before use.  Calls whose work overlaps
+ *     on the GPU (other streams, other threads, other handles) race on it:
+ *     serialise them.
+ *   - WLB_ERR_ARG if n_surface > WLB_NOALLOC_MAX_SURFACE or n_steps < 0;
+ *     WLB_ERR_STATE before wlb_init; WLB_ERR_UNSTABLE on non-finite sums.
+ */
+#define WLB_NOALLOC_MAX_SURFACE 8192
+wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, double force_out[3]);
+
 /* Sizes and counters of a handle. */
 wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
 

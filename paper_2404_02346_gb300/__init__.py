@@ -72,6 +72,7 @@ _SIGNATURES = {
     "wlb_mask": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ubyte)]),
     "wlb_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(Info)]),
     "wlb_destroy": (ctypes.c_int, [_VP]),
+    "wlb_average_noalloc": (ctypes.c_int, [_VP, ctypes.c_longlong, _DP]),
     "wlb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "wlb_last_error": (ctypes.c_char_p, [_VP]),
 }

@@ -1,0 +1,25 @@
+// Definition of the opaque wlb_handle, shared by the C-ABI translation units.
+#pragma once
+#include "../../include/wlb.h"
+#include "wlb_internal.cuh"
+
+struct wlb_handle {
+    wlb_params p;
+    wlb::Geometry g;
+    wlb::Buffers b;
+    bool f64 = false;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;  // private stream used only to capture graphs
+    void *owned = nullptr;           // workspace allocated by the library, if any
+    double *host_out = nullptr;      // pinned: force[4] + error flag
+    int src = 0;                     // population buffer holding the current state
+    bool initialised = false;
+    long long period = 0, n_steps = 0, n_window = 0;
+    long long steps_done = 0, samples_done = 0, samples_in_period = 0;
+    cudaGraphExec_t graph_free[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph_sampled[2] = {nullptr, nullptr};
+    bool vector_path = false;
+    char err[512] = {0};
+};
+
