@@ -135,6 +135,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_totals(local_ms, local_units, world, device=None):
+    """Whole-job figures for N independent replicas: the slowest rank's time and
+    the units all ranks processed (max / sum all-reduce; gloo or NCCL)."""
+    if world <= 1:
+        return float(local_ms), float(local_units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def cpu_baseline(prob, target_s=15.0, steps=None):
     """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
     the full lattice for a few LB steps, a third of them sampled."""
@@ -243,13 +257,9 @@ def run_gpu(args, prob):
     clk = clocks.stop()
     ms = start.elapsed_time(end)
     k1_ms = sum(a.elapsed_time(b) for a, b in k1) / (args.steps * n_free)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    lu = cells * n_steps * args.steps * world
+    ms, lu = job_totals(ms, cells * n_steps * args.steps, world, device="cuda")
     glups = lu / (ms * 1e-3) / 1e9
-    forces_per_s = args.steps * world / (ms * 1e-3)
+    forces_per_s = lu / (cells * n_steps) / (ms * 1e-3)
 
     # end to end through the public API: host parameters in, host force out
     e2e_steps = max(1, min(args.steps, 2))
