@@ -280,13 +280,14 @@ def run_gpu(args, prob):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    traffic = _traffic(_kernel_sha())
+    traffic = _traffic(_kernel_sha()) if args.precision == "f32" else None
     launches = args.steps * (2 + n_free + 2 * n_window + n_avg + 1)
     if rank == 0:
         line = {
             "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f32": "f32", "f64": "f64", "f16": "f16 storage, f32 arithmetic"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": cells, "lb_steps_per_force": n_steps,
                        "window_steps": n_window, "kappa_ratio": prob.get("kappa"),
@@ -296,7 +297,7 @@ def run_gpu(args, prob):
             "force": [float(v) for v in F],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "update_rows<float,3,2>", "bytes_per_cell": bpu,
+                         "kernel": "update_rows (%s storage)" % args.precision, "bytes_per_cell": bpu,
                          "avg_launch_us": k1_ms * 1e3, "peak_source": peak_src + " hbm_gbs"},
             "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
@@ -337,8 +338,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short pass for ncu captures")
     ap.add_argument("--profile-steps", type=int, default=64)
+    ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"],
+                    help="population storage (the benchmark workload is FP32)")
     args = ap.parse_args()
-    prob = workloads.sphere_3d(seed=args.seed)
+    prob = workloads.sphere_3d(seed=args.seed, precision=args.precision)
     if args.profile:
         run_profile(args, prob)
     elif args.impl == "reference":

@@ -53,7 +53,10 @@ typedef enum {
 } wlb_status;
 
 typedef enum { WLB_D2Q5 = 0, WLB_D3Q7 = 1 } wlb_lattice;          /* Fig. 8   */
-typedef enum { WLB_POP_F32 = 0, WLB_POP_F64 = 1 } wlb_precision;  /* storage and arithmetic of the populations */
+/* Storage and arithmetic of the populations: FP32, FP64, or FP16 storage of
+ * f / p_a (the deviation from the rest state f = 0, scaled to O(1)) with FP32
+ * arithmetic, running sums and sound-speed field. */
+typedef enum { WLB_POP_F32 = 0, WLB_POP_F64 = 1, WLB_POP_F16 = 2 } wlb_precision;
 
 /*
  * Problem statement (Sec. VII and Table I; Eq. 79 for the object).
@@ -78,7 +81,7 @@ typedef enum { WLB_POP_F32 = 0, WLB_POP_F64 = 1 } wlb_precision;  /* storage and
  *   n_surface      N surface elements: equal arcs in 2D, Fibonacci points in 3D.
  *   n_periods      total run length in periods T.
  *   n_avg_periods  the last n_avg_periods periods are averaged (<= n_periods).
- *   precision      WLB_POP_F32 or WLB_POP_F64.
+ *   precision      WLB_POP_F32, WLB_POP_F64 or WLB_POP_F16 (p_a != 0).
  *
  * The object, its interface band and the interpolation stencil must fit in
  * half the box along every axis (minimum-image distances must be unique).
@@ -108,7 +111,8 @@ typedef struct {
     long long steps_done;       /* steps since the last wlb_init (0 if none)    */
     long long samples_done;     /* steps sampled since the last wlb_init        */
     double bytes_per_update;    /* algorithmic HBM bytes of one cell update:
-                                   2 q pop_bytes + 1 (class byte)              */
+                                   2 q pop_bytes + 1 (class byte); pop_bytes is
+                                   4, 8 or 2                                   */
     int vector_path;            /* 1 if the row-vectorised update kernel is used */
 } wlb_info;
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libwlb.so")
 
 WLB_OK, WLB_ERR_ARG, WLB_ERR_UNSTABLE, WLB_ERR_CUDA, WLB_ERR_OOM, WLB_ERR_STATE = range(6)
 WLB_D2Q5, WLB_D3Q7 = 0, 1
-WLB_POP_F32, WLB_POP_F64 = 0, 1
+WLB_POP_F32, WLB_POP_F64, WLB_POP_F16 = 0, 1, 2
 
 
 class WlbError(RuntimeError):
@@ -121,7 +121,7 @@ def params_from_problem(prob, precision=None):
     p.n_periods = int(prob["n_steps"] // T)
     p.n_avg_periods = int(prob["n_window"] // T)
     prec = precision or prob.get("precision", "f32")
-    p.precision = WLB_POP_F64 if prec == "f64" else WLB_POP_F32
+    p.precision = {"f32": WLB_POP_F32, "f64": WLB_POP_F64, "f16": WLB_POP_F16}[prec]
     return p
 
 

@@ -67,6 +67,7 @@ Geometry make_geometry(const wlb_params *p) {
     g.interface_d = p->interface_d;
     g.surface_radius = p->surface_radius;
     g.band_half = 20.0 * p->interface_d;
+    g.pop_scale = p->precision == WLB_POP_F16 ? 1.0 / p->p_a : 1.0;
     g.n_surface = p->n_surface;
     g.stencil = g.dim == 3 ? 27 : 9;
     return g;
@@ -74,9 +75,14 @@ Geometry make_geometry(const wlb_params *p) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+wlb::Prec prec_of(const wlb_params *p) {
+    return p->precision == WLB_POP_F64 ? wlb::Prec::F64
+                                       : (p->precision == WLB_POP_F16 ? wlb::Prec::F16 : wlb::Prec::F32);
+}
+
 // Carve the workspace; with base == nullptr only the size is computed.
-size_t layout(const Geometry &g, bool f64, char *base, Buffers *b) {
-    const size_t T = f64 ? 8 : 4;
+size_t layout(const Geometry &g, wlb::Prec prec, char *base, Buffers *b) {
+    const size_t P = wlb::pop_bytes(prec), T = wlb::real_bytes(prec);
     const size_t nc = (size_t)g.ncell, N = (size_t)g.n_surface, S = (size_t)g.stencil;
     size_t off = 0;
     auto take = [&](size_t bytes) -> void * {
@@ -85,8 +91,8 @@ size_t layout(const Geometry &g, bool f64, char *base, Buffers *b) {
         return ptr;
     };
     Buffers t{};
-    t.pop[0] = take(g.q * nc * T);
-    t.pop[1] = take(g.q * nc * T);
+    t.pop[0] = take(g.q * nc * P);
+    t.pop[1] = take(g.q * nc * P);
     t.cls = (uint8_t *)take(nc);
     t.c2 = take(nc * T);
     t.pts = (double *)take(N * 7 * sizeof(double));
@@ -117,14 +123,14 @@ cudaError_t issue_period(wlb_handle *h, int start, bool sampled, cudaStream_t s)
     for (long long t = 0; t < h->period; ++t) {
         cudaError_t e;
         if (sampled) {
-            e = wlb::launch_sample(h->g, h->b, h->f64, cur, s);
+            e = wlb::launch_sample(h->g, h->b, h->prec, cur, s);
             if (e != cudaSuccess) return e;
         }
-        e = wlb::launch_update(h->g, h->b, h->f64, cur, s, nullptr);
+        e = wlb::launch_update(h->g, h->b, h->prec, cur, s, nullptr);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
-    if (sampled) return wlb::launch_fold(h->g, h->b, h->f64, s);
+    if (sampled) return wlb::launch_fold(h->g, h->b, h->prec, s);
     return cudaSuccess;
 }
 
@@ -168,7 +174,8 @@ const char *wlb_last_error(const wlb_handle *h) { return h ? h->err : ""; }
 wlb_status wlb_validate(const wlb_params *p) {
     if (!p) return WLB_ERR_ARG;
     if (p->lattice != WLB_D2Q5 && p->lattice != WLB_D3Q7) return WLB_ERR_ARG;
-    if (p->precision != WLB_POP_F32 && p->precision != WLB_POP_F64) return WLB_ERR_ARG;
+    if (p->precision != WLB_POP_F32 && p->precision != WLB_POP_F64 && p->precision != WLB_POP_F16)
+        return WLB_ERR_ARG;
     const int D = dim_of(p);
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return WLB_ERR_ARG;
     if (D == 2 && p->nz != 1) return WLB_ERR_ARG;
@@ -177,6 +184,7 @@ wlb_status wlb_validate(const wlb_params *p) {
     if (!(p->c0 > 0) || !(p->cp > 0) || !(p->rho0 > 0)) return WLB_ERR_ARG;
     if (!(D * p->c0 * p->c0 < 1.0) || !(D * p->cp * p->cp < 1.0)) return WLB_ERR_ARG;
     if (!std::isfinite(p->p_a) || !std::isfinite(p->antinode)) return WLB_ERR_ARG;
+    if (p->precision == WLB_POP_F16 && !(p->p_a != 0.0)) return WLB_ERR_ARG;  // storage scale 1/p_a
     if (!(p->wavelength > 0) || !whole(p->wavelength / p->c0)) return WLB_ERR_ARG;
     const int n[3] = {p->nx, p->ny, p->nz};
     if (!whole(n[p->wave_axis] / p->wavelength)) return WLB_ERR_ARG;
@@ -199,7 +207,7 @@ wlb_status wlb_workspace_bytes(const wlb_params *p, size_t *bytes) {
     if (!bytes) return WLB_ERR_ARG;
     wlb_status s = wlb_validate(p);
     if (s != WLB_OK) return s;
-    *bytes = layout(make_geometry(p), p->precision == WLB_POP_F64, nullptr, nullptr);
+    *bytes = layout(make_geometry(p), prec_of(p), nullptr, nullptr);
     return WLB_OK;
 }
 
@@ -213,13 +221,13 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
     if (!h) return WLB_ERR_OOM;
     h->p = *p;
     h->g = make_geometry(p);
-    h->f64 = p->precision == WLB_POP_F64;
+    h->prec = prec_of(p);
     h->stream = (cudaStream_t)stream;
     h->period = (long long)std::nearbyint(p->wavelength / p->c0);
     h->n_steps = h->period * p->n_periods;
     h->n_window = h->period * p->n_avg_periods;
-    h->vector_path = wlb::update_is_vectorised(h->g, h->f64);
-    const size_t need = layout(h->g, h->f64, nullptr, nullptr);
+    h->vector_path = wlb::update_is_vectorised(h->g, h->prec);
+    const size_t need = layout(h->g, h->prec, nullptr, nullptr);
     char *base = (char *)device_workspace;
     if (base && workspace_bytes < need) {  // checked before any CUDA call
         delete h;
@@ -239,7 +247,7 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
         }
         base = (char *)h->owned;
     }
-    layout(h->g, h->f64, base, &h->b);
+    layout(h->g, h->prec, base, &h->b);
     e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->host_out, 8 * sizeof(double), cudaHostAllocDefault);
     if (e != cudaSuccess) {
@@ -253,7 +261,7 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
 wlb_status wlb_init(wlb_handle *h) {
     if (!h) return WLB_ERR_ARG;
     DeviceGuard dg(h->device);
-    WLB_CUDA(h, wlb::launch_setup(h->g, h->b, h->f64, h->stream), "setup kernels");
+    WLB_CUDA(h, wlb::launch_setup(h->g, h->b, h->prec, h->stream), "setup kernels");
     h->src = 0;
     h->steps_done = h->samples_done = h->samples_in_period = 0;
     h->initialised = true;
@@ -277,14 +285,14 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
             n -= h->period;
             continue;
         }
-        if (sampled) WLB_CUDA(h, wlb::launch_sample(h->g, h->b, h->f64, h->src, h->stream), "sample kernel");
-        WLB_CUDA(h, wlb::launch_update(h->g, h->b, h->f64, h->src, h->stream, nullptr), "update kernel");
+        if (sampled) WLB_CUDA(h, wlb::launch_sample(h->g, h->b, h->prec, h->src, h->stream), "sample kernel");
+        WLB_CUDA(h, wlb::launch_update(h->g, h->b, h->prec, h->src, h->stream, nullptr), "update kernel");
         h->src ^= 1;
         h->steps_done += 1;
         if (sampled) {
             h->samples_done += 1;
             if (++h->samples_in_period == h->period) {
-                WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->f64, h->stream), "fold kernel");
+                WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->prec, h->stream), "fold kernel");
                 h->samples_in_period = 0;
             }
         }
@@ -303,7 +311,7 @@ wlb_status wlb_force(wlb_handle *h, double force_out[3]) {
         return WLB_OK;
     }
     if (h->samples_in_period > 0) {
-        WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->f64, h->stream), "fold kernel");
+        WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->prec, h->stream), "fold kernel");
         h->samples_in_period = 0;
     }
     WLB_CUDA(h, wlb::launch_force(h->g, h->b, (double)h->samples_done, h->stream), "force kernel");
@@ -335,7 +343,7 @@ wlb_status wlb_fields(wlb_handle *h, double *p1_out, double *u1_out) {
     const long long nc = h->g.ncell, chunk = h->b.stage_cells;
     for (long long first = 0; first < nc; first += chunk) {
         const long long count = nc - first < chunk ? nc - first : chunk;
-        WLB_CUDA(h, wlb::launch_fields(h->g, h->b, h->f64, h->src, first, count, h->stream), "fields kernel");
+        WLB_CUDA(h, wlb::launch_fields(h->g, h->b, h->prec, h->src, first, count, h->stream), "fields kernel");
         if (p1_out)
             WLB_CUDA(h, cudaMemcpyAsync(p1_out + first, h->b.stage, count * sizeof(double),
                                         cudaMemcpyDeviceToHost, h->stream), "p1 copy");
@@ -381,7 +389,7 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out) {
     out->n_window = h->n_window;
     out->steps_done = h->steps_done;
     out->samples_done = h->samples_done;
-    out->bytes_per_update = 2.0 * h->g.q * (h->f64 ? 8.0 : 4.0) + 1.0;
+    out->bytes_per_update = 2.0 * h->g.q * (double)wlb::pop_bytes(h->prec) + 1.0;
     out->vector_path = h->vector_path ? 1 : 0;
     return WLB_OK;
 }

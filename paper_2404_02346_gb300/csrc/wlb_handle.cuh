@@ -7,7 +7,7 @@ struct wlb_handle {
     wlb_params p;
     wlb::Geometry g;
     wlb::Buffers b;
-    bool f64 = false;
+    wlb::Prec prec = wlb::Prec::F32;
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;  // private stream used only to capture graphs

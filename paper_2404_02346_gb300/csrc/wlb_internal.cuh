@@ -9,6 +9,14 @@ namespace wlb {
 // Cell classes (the byte field read by the update kernel).
 enum : uint8_t { CELL_FLUID = 0, CELL_OBJECT = 1, CELL_BAND = 2 };
 
+// Population storage: FP32, FP64, or FP16 of f / p_a with FP32 arithmetic.
+enum class Prec { F32, F64, F16 };
+
+// Bytes of one stored population value and of one "real" value (sound speed,
+// weights, running sums) for a storage precision.
+inline size_t pop_bytes(Prec p) { return p == Prec::F64 ? 8 : (p == Prec::F32 ? 4 : 2); }
+inline size_t real_bytes(Prec p) { return p == Prec::F64 ? 8 : 4; }
+
 // Problem description as the kernels see it (passed by value).
 struct Geometry {
     int dim, q;            // 2 or 3; 5 or 7
@@ -20,20 +28,21 @@ struct Geometry {
     double center[3];
     double radius, interface_d, surface_radius;
     double band_half;      // class threshold on |x-r0|^2 - R^2 (20 d)
+    double pop_scale;      // stored populations are f * pop_scale (1, or 1/p_a for FP16)
     int n_surface;
     int stencil;           // 3^dim
 };
 
 // Device buffers carved from one workspace.
 struct Buffers {
-    void *pop[2];          // populations, q * ncell of T each
+    void *pop[2];          // populations, q * ncell stored values each
     uint8_t *cls;          // ncell
-    void *c2;              // ncell of T: sound speed squared (read for band cells)
+    void *c2;              // ncell reals: sound speed squared (read for band cells)
     double *pts;           // n_surface * 7
     int4 *st_xyz;          // n_surface * stencil: wrapped cell coordinates
-    void *st_w;            // n_surface * stencil * 2 of T: (delta c^2, delta / rho0)
-    void *nrm;             // n_surface * 4 of T: normal (x, y, z, 0)
-    void *acc;             // n_surface * 5 of T: running sums within a period
+    void *st_w;            // n_surface * stencil * 2 reals: (delta c^2, delta / rho0)
+    void *nrm;             // n_surface * 4 reals: normal (x, y, z, 0)
+    void *acc;             // n_surface * 5 reals: running sums within a period
     double *acc64;         // n_surface * 5: folded sums
     double *force;         // 4 doubles
     int *err;              // 1 int: non-finite accumulator seen
@@ -42,14 +51,14 @@ struct Buffers {
 };
 
 // Launchers (each TU owns its kernels).  All return cudaGetLastError().
-cudaError_t launch_setup(const Geometry &g, const Buffers &b, bool f64, cudaStream_t s);
-cudaError_t launch_update(const Geometry &g, const Buffers &b, bool f64, int src, cudaStream_t s,
+cudaError_t launch_setup(const Geometry &g, const Buffers &b, Prec p, cudaStream_t s);
+cudaError_t launch_update(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s,
                           bool *vector_path);
-cudaError_t launch_sample(const Geometry &g, const Buffers &b, bool f64, int src, cudaStream_t s);
-cudaError_t launch_fold(const Geometry &g, const Buffers &b, bool f64, cudaStream_t s);
+cudaError_t launch_sample(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s);
+cudaError_t launch_fold(const Geometry &g, const Buffers &b, Prec p, cudaStream_t s);
 cudaError_t launch_force(const Geometry &g, const Buffers &b, double n_window, cudaStream_t s);
-cudaError_t launch_fields(const Geometry &g, const Buffers &b, bool f64, int src,
+cudaError_t launch_fields(const Geometry &g, const Buffers &b, Prec p, int src,
                           long long first_cell, long long count, cudaStream_t s);
-bool update_is_vectorised(const Geometry &g, bool f64);
+bool update_is_vectorised(const Geometry &g, Prec p);
 
 }  // namespace wlb

@@ -70,7 +70,7 @@ extern "C" wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, doub
         cudaError_t e = scratch_address(h->device, &base);
         if (e != cudaSuccess) { st = note(h, WLB_ERR_CUDA, "cudaGetSymbolAddress", e); break; }
         const int N = h->g.n_surface;
-        const size_t tb = h->f64 ? sizeof(double) : sizeof(float);
+        const size_t tb = wlb::real_bytes(h->prec);
         wlb::Buffers b = h->b;  // populations, classes, stencils: the handle's
         b.acc = base;
         b.acc64 = (double *)((char *)base + kSumBytes);
@@ -85,15 +85,15 @@ extern "C" wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, doub
         }
         long long in_period = 0;
         for (long long t = 0; t < n_steps && st == WLB_OK; ++t) {
-            if ((e = wlb::launch_sample(h->g, b, h->f64, h->src, h->stream)) != cudaSuccess ||
-                (e = wlb::launch_update(h->g, b, h->f64, h->src, h->stream, nullptr)) != cudaSuccess) {
+            if ((e = wlb::launch_sample(h->g, b, h->prec, h->src, h->stream)) != cudaSuccess ||
+                (e = wlb::launch_update(h->g, b, h->prec, h->src, h->stream, nullptr)) != cudaSuccess) {
                 st = note(h, WLB_ERR_CUDA, "step kernels", e);
                 break;
             }
             h->src ^= 1;
             h->steps_done += 1;
             if (++in_period == h->period) {
-                if ((e = wlb::launch_fold(h->g, b, h->f64, h->stream)) != cudaSuccess)
+                if ((e = wlb::launch_fold(h->g, b, h->prec, h->stream)) != cudaSuccess)
                     st = note(h, WLB_ERR_CUDA, "fold kernel", e);
                 in_period = 0;
             }
@@ -104,7 +104,7 @@ extern "C" wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, doub
             force_out[0] = force_out[1] = force_out[2] = 0.0;
             break;
         }
-        if (in_period > 0 && (e = wlb::launch_fold(h->g, b, h->f64, h->stream)) != cudaSuccess) {
+        if (in_period > 0 && (e = wlb::launch_fold(h->g, b, h->prec, h->stream)) != cudaSuccess) {
             st = note(h, WLB_ERR_CUDA, "fold kernel", e);
             break;
         }

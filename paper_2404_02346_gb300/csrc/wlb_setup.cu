@@ -2,6 +2,8 @@
 // standing-wave initial condition imposed through the equilibrium (Sec. V,
 // Eqs. 71-72), surface elements (Sec. VI) and the interpolation stencils with
 // the three-point kernel of Eq. (82).
+#include <cuda_fp16.h>
+
 #include "wlb_internal.cuh"
 
 namespace wlb {
@@ -58,11 +60,16 @@ __device__ double incident_pressure(const Geometry &g, int x, int y, int z) {
     return g.p_a * cos(2.0 * kPi * s / g.wavelength);
 }
 
+// Conversion of an FP64 value to the storage type (round to nearest).
+template <typename S> __device__ __forceinline__ S to_store(double v) { return (S)v; }
+template <> __device__ __forceinline__ __half to_store<__half>(double v) { return __double2half(v); }
+
 // Populations are stored post-collision and pulled by the next update, so the
 // stored value of direction i at cell x is the value that arrives at x + v_i:
-// the equilibrium (Eq. 71 with rho1 = p1/c^2, J1 = 0) of the cell x + v_i.
-template <typename T>
-__global__ void setup_cells(Geometry g, T *__restrict__ pop, uint8_t *__restrict__ cls,
+// the equilibrium (Eq. 71 with rho1 = p1/c^2, J1 = 0) of the cell x + v_i,
+// times the storage scale.
+template <typename S, typename T>
+__global__ void setup_cells(Geometry g, S *__restrict__ pop, uint8_t *__restrict__ cls,
                             T *__restrict__ c2f) {
     long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= g.ncell) return;
@@ -75,14 +82,14 @@ __global__ void setup_cells(Geometry g, T *__restrict__ pop, uint8_t *__restrict
     double c2 = sound_speed_sq(g, x, y, z);
     c2f[id] = (T)c2;
     double p = incident_pressure(g, x, y, z);
-    pop[id] = (T)((p / c2) * (1.0 - g.dim * c2));        // f_0^eq = rho1 (1 - D c^2)
+    pop[id] = to_store<S>((p / c2) * (1.0 - g.dim * c2) * g.pop_scale);  // f_0^eq = rho1 (1 - D c^2)
     for (int i = 1; i < g.q; ++i) {
         int a = (i - 1) >> 1;
         int v = ((i - 1) & 1) ? -1 : 1;
         int c[3] = {x, y, z};
         c[a] = wrap_index(c[a] + v, g.n[a]);
         double pn = incident_pressure(g, c[0], c[1], c[2]);
-        pop[(long long)i * g.ncell + id] = (T)(0.5 * pn);  // f_i^eq = c^2 rho1 / 2
+        pop[(long long)i * g.ncell + id] = to_store<S>(0.5 * pn * g.pop_scale);  // f_i^eq = c^2 rho1 / 2
     }
 }
 
@@ -183,11 +190,11 @@ __global__ void setup_surface(Geometry g, double *__restrict__ pts, T *__restric
             }
 }
 
-template <typename T>
+template <typename S, typename T>
 cudaError_t setup_impl(const Geometry &g, const Buffers &b, cudaStream_t s) {
     const int tb = 256;
     long long blocks = (g.ncell + tb - 1) / tb;
-    setup_cells<T><<<(unsigned)blocks, tb, 0, s>>>(g, (T *)b.pop[0], b.cls, (T *)b.c2);
+    setup_cells<S, T><<<(unsigned)blocks, tb, 0, s>>>(g, (S *)b.pop[0], b.cls, (T *)b.c2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (g.n_surface > 0) {
@@ -207,8 +214,12 @@ cudaError_t setup_impl(const Geometry &g, const Buffers &b, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_setup(const Geometry &g, const Buffers &b, bool f64, cudaStream_t s) {
-    return f64 ? setup_impl<double>(g, b, s) : setup_impl<float>(g, b, s);
+cudaError_t launch_setup(const Geometry &g, const Buffers &b, Prec p, cudaStream_t s) {
+    switch (p) {
+        case Prec::F64: return setup_impl<double, double>(g, b, s);
+        case Prec::F16: return setup_impl<__half, float>(g, b, s);
+        default: return setup_impl<float, float>(g, b, s);
+    }
 }
 
 }  // namespace wlb

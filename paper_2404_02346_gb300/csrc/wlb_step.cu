@@ -14,6 +14,10 @@
 //     f*_0  = 2 rho1 (1 - D c^2) - f_0,
 //     f*_+a = c^2 rho1 + J_a - f_+a = c^2 rho1 - f_-a,
 //     f*_-a = c^2 rho1 - J_a - f_-a = c^2 rho1 - f_+a.
+// The update is linear in f, so populations may be stored scaled (FP16 stores
+// f / p_a); the scale only enters the setup, the fold and the read-back.
+#include <cuda_fp16.h>
+
 #include "wlb_internal.cuh"
 
 namespace wlb {
@@ -21,25 +25,71 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// 16-byte vector access with streaming cache hints: every population is read
-// once and written once per step.
-__device__ __forceinline__ void load16(const float *p, float (&v)[4]) {
-    float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-}
-__device__ __forceinline__ void load16(const double *p, double (&v)[2]) {
-    double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
-    v[0] = t.x; v[1] = t.y;
-}
-__device__ __forceinline__ void store16(float *p, const float (&v)[4]) {
-    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
-}
-__device__ __forceinline__ void store16(double *p, const double (&v)[2]) {
-    __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
-}
+// Storage traits: R is the arithmetic type, W the values per 16-byte vector.
+// Vector accesses use streaming cache hints: every population is read once and
+// written once per step.
+template <typename S> struct Store;
+
+template <> struct Store<float> {
+    using R = float;
+    static constexpr int W = 4;
+    __device__ static void load(const float *p, float (&v)[4]) {
+        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ static void store(float *p, const float (&v)[4]) {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
+    __device__ static float get(const float *p) { return *p; }
+    __device__ static void put(float *p, float v) { *p = v; }
+};
+
+template <> struct Store<double> {
+    using R = double;
+    static constexpr int W = 2;
+    __device__ static void load(const double *p, double (&v)[2]) {
+        const double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    }
+    __device__ static void store(double *p, const double (&v)[2]) {
+        __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+    }
+    __device__ static double get(const double *p) { return *p; }
+    __device__ static void put(double *p, double v) { *p = v; }
+};
+
+template <> struct Store<__half> {
+    using R = float;
+    static constexpr int W = 8;
+    __device__ static void load(const __half *p, float (&v)[8]) {
+        const uint4 t = __ldcs(reinterpret_cast<const uint4 *>(p));
+        const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h;
+            memcpy(&h, &w[i], 4);
+            const float2 f = __half22float2(h);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    }
+    __device__ static void store(__half *p, const float (&v)[8]) {
+        unsigned w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+            memcpy(&w[i], &h, 4);
+        }
+        __stcs(reinterpret_cast<uint4 *>(p), make_uint4(w[0], w[1], w[2], w[3]));
+    }
+    __device__ static float get(const __half *p) { return __half2float(*p); }
+    __device__ static void put(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
 template <int W>
-__device__ __forceinline__ uint32_t load_classes(const uint8_t *p) {
-    if constexpr (W == 4) return *reinterpret_cast<const uint32_t *>(p);
+__device__ __forceinline__ unsigned long long load_classes(const uint8_t *p) {
+    if constexpr (W == 8) return *reinterpret_cast<const unsigned long long *>(p);
+    else if constexpr (W == 4) return *reinterpret_cast<const uint32_t *>(p);
     else return *reinterpret_cast<const uint16_t *>(p);
 }
 
@@ -48,12 +98,14 @@ __device__ __forceinline__ uint32_t load_classes(const uint8_t *p) {
 // Every population row is read with aligned 16-byte loads: the +-y and +-z
 // neighbours are whole rows, and the +-x shift (including the periodic wrap at
 // the row ends) is done with warp shuffles, so no element is loaded twice.
-template <typename T, int D, int CH>
-__global__ void __launch_bounds__(256) update_rows(const T *__restrict__ src, T *__restrict__ dst,
+template <typename S, int D, int CH>
+__global__ void __launch_bounds__(256) update_rows(const S *__restrict__ src, S *__restrict__ dst,
                                                    const uint8_t *__restrict__ cls,
-                                                   const T *__restrict__ c2f, int nx, int ny, int nz,
-                                                   long long ncell, T c0sq, T cpsq) {
-    constexpr int W = 16 / sizeof(T);
+                                                   const typename Store<S>::R *__restrict__ c2f, int nx,
+                                                   int ny, int nz, long long ncell,
+                                                   typename Store<S>::R c0sq, typename Store<S>::R cpsq) {
+    using R = typename Store<S>::R;
+    constexpr int W = Store<S>::W;
     constexpr int Q = 2 * D + 1;
     const int lane = threadIdx.x & 31;
     const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -73,25 +125,25 @@ __global__ void __launch_bounds__(256) update_rows(const T *__restrict__ src, T 
         rzp = ((long long)zp * ny + y) * nx;
     }
 
-    T f[Q][CH][W];
-    uint32_t cl[CH];
+    R f[Q][CH][W];
+    unsigned long long cl[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
         const int x0 = (c * 32 + lane) * W;
-        load16(src + r0 + x0, f[0][c]);
-        load16(src + ncell + r0 + x0, f[1][c]);
-        load16(src + 2 * ncell + r0 + x0, f[2][c]);
-        load16(src + 3 * ncell + rym + x0, f[3][c]);
-        load16(src + 4 * ncell + ryp + x0, f[4][c]);
+        Store<S>::load(src + r0 + x0, f[0][c]);
+        Store<S>::load(src + ncell + r0 + x0, f[1][c]);
+        Store<S>::load(src + 2 * ncell + r0 + x0, f[2][c]);
+        Store<S>::load(src + 3 * ncell + rym + x0, f[3][c]);
+        Store<S>::load(src + 4 * ncell + ryp + x0, f[4][c]);
         if (D == 3) {
-            load16(src + 5 * ncell + rzm + x0, f[5][c]);
-            load16(src + 6 * ncell + rzp + x0, f[6][c]);
+            Store<S>::load(src + 5 * ncell + rzm + x0, f[5][c]);
+            Store<S>::load(src + 6 * ncell + rzp + x0, f[6][c]);
         }
         cl[c] = load_classes<W>(cls + r0 + x0);
     }
 
     // The +x population arriving at x left x-1; the -x one left x+1.
-    T up[CH], dn[CH];
+    R up[CH], dn[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
         up[c] = __shfl_sync(kFull, f[1][c][W - 1], (lane + 31) & 31);
@@ -101,7 +153,7 @@ __global__ void __launch_bounds__(256) update_rows(const T *__restrict__ src, T 
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
         const int x0 = (c * 32 + lane) * W;
-        T fpx[W], fmx[W];
+        R fpx[W], fmx[W];
         fpx[0] = lane == 0 ? up[(c + CH - 1) % CH] : up[c];
 #pragma unroll
         for (int e = 1; e < W; ++e) fpx[e] = f[1][c][e - 1];
@@ -109,15 +161,15 @@ __global__ void __launch_bounds__(256) update_rows(const T *__restrict__ src, T 
         for (int e = 0; e < W - 1; ++e) fmx[e] = f[2][c][e + 1];
         fmx[W - 1] = lane == 31 ? dn[(c + 1) % CH] : dn[c];
 
-        T o[Q][W];
+        R o[Q][W];
 #pragma unroll
         for (int e = 0; e < W; ++e) {
-            const uint32_t k = (cl[c] >> (8 * e)) & 0xffu;
-            const T c2 = k == CELL_FLUID ? c0sq : (k == CELL_OBJECT ? cpsq : c2f[r0 + x0 + e]);
-            T rho = f[0][c][e] + fpx[e] + fmx[e] + f[3][c][e] + f[4][c][e];
+            const unsigned k = (unsigned)(cl[c] >> (8 * e)) & 0xffu;
+            const R c2 = k == CELL_FLUID ? c0sq : (k == CELL_OBJECT ? cpsq : c2f[r0 + x0 + e]);
+            R rho = f[0][c][e] + fpx[e] + fmx[e] + f[3][c][e] + f[4][c][e];
             if (D == 3) rho += f[5][c][e] + f[6][c][e];
-            const T eq = c2 * rho;
-            o[0][e] = T(2) * (rho - T(D) * eq) - f[0][c][e];
+            const R eq = c2 * rho;
+            o[0][e] = R(2) * (rho - R(D) * eq) - f[0][c][e];
             o[1][e] = eq - fmx[e];
             o[2][e] = eq - fpx[e];
             o[3][e] = eq - f[4][c][e];
@@ -128,16 +180,18 @@ __global__ void __launch_bounds__(256) update_rows(const T *__restrict__ src, T 
             }
         }
 #pragma unroll
-        for (int i = 0; i < Q; ++i) store16(dst + i * ncell + r0 + x0, o[i]);
+        for (int i = 0; i < Q; ++i) Store<S>::store(dst + i * ncell + r0 + x0, o[i]);
     }
 }
 
 // Any lattice shape: one thread per cell, scalar accesses.
-template <typename T, int D>
-__global__ void __launch_bounds__(256) update_cells(const T *__restrict__ src, T *__restrict__ dst,
+template <typename S, int D>
+__global__ void __launch_bounds__(256) update_cells(const S *__restrict__ src, S *__restrict__ dst,
                                                     const uint8_t *__restrict__ cls,
-                                                    const T *__restrict__ c2f, int nx, int ny, int nz,
-                                                    long long ncell, T c0sq, T cpsq) {
+                                                    const typename Store<S>::R *__restrict__ c2f, int nx,
+                                                    int ny, int nz, long long ncell,
+                                                    typename Store<S>::R c0sq, typename Store<S>::R cpsq) {
+    using R = typename Store<S>::R;
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= ncell) return;
     const int x = (int)(id % nx);
@@ -147,56 +201,59 @@ __global__ void __launch_bounds__(256) update_cells(const T *__restrict__ src, T
     const long long row = id - x;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    const T f0 = src[id];
-    const T fpx = src[ncell + row + xm];
-    const T fmx = src[2 * ncell + row + xp];
-    const T fpy = src[3 * ncell + ((long long)z * ny + ym) * nx + x];
-    const T fmy = src[4 * ncell + ((long long)z * ny + yp) * nx + x];
-    T fpz = 0, fmz = 0;
+    const R f0 = Store<S>::get(src + id);
+    const R fpx = Store<S>::get(src + ncell + row + xm);
+    const R fmx = Store<S>::get(src + 2 * ncell + row + xp);
+    const R fpy = Store<S>::get(src + 3 * ncell + ((long long)z * ny + ym) * nx + x);
+    const R fmy = Store<S>::get(src + 4 * ncell + ((long long)z * ny + yp) * nx + x);
+    R fpz = 0, fmz = 0;
     if (D == 3) {
         const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-        fpz = src[5 * ncell + ((long long)zm * ny + y) * nx + x];
-        fmz = src[6 * ncell + ((long long)zp * ny + y) * nx + x];
+        fpz = Store<S>::get(src + 5 * ncell + ((long long)zm * ny + y) * nx + x);
+        fmz = Store<S>::get(src + 6 * ncell + ((long long)zp * ny + y) * nx + x);
     }
     const uint8_t k = cls[id];
-    const T c2 = k == CELL_FLUID ? c0sq : (k == CELL_OBJECT ? cpsq : c2f[id]);
-    T rho = f0 + fpx + fmx + fpy + fmy;
+    const R c2 = k == CELL_FLUID ? c0sq : (k == CELL_OBJECT ? cpsq : c2f[id]);
+    R rho = f0 + fpx + fmx + fpy + fmy;
     if (D == 3) rho += fpz + fmz;
-    const T eq = c2 * rho;
-    dst[id] = T(2) * (rho - T(D) * eq) - f0;
-    dst[ncell + id] = eq - fmx;
-    dst[2 * ncell + id] = eq - fpx;
-    dst[3 * ncell + id] = eq - fmy;
-    dst[4 * ncell + id] = eq - fpy;
+    const R eq = c2 * rho;
+    Store<S>::put(dst + id, R(2) * (rho - R(D) * eq) - f0);
+    Store<S>::put(dst + ncell + id, eq - fmx);
+    Store<S>::put(dst + 2 * ncell + id, eq - fpx);
+    Store<S>::put(dst + 3 * ncell + id, eq - fmy);
+    Store<S>::put(dst + 4 * ncell + id, eq - fpy);
     if (D == 3) {
-        dst[5 * ncell + id] = eq - fmz;
-        dst[6 * ncell + id] = eq - fpz;
+        Store<S>::put(dst + 5 * ncell + id, eq - fmz);
+        Store<S>::put(dst + 6 * ncell + id, eq - fpz);
     }
 }
 
-// rho1 and J1 at cell (x, y, z) at the current time: the pull-sum of the stored
-// post-collision populations (Eq. 62 applied after the advection of Eq. 64).
-template <typename T>
-__device__ __forceinline__ void pulled_moments(const Geometry &g, const T *__restrict__ src, int x,
-                                               int y, int z, T &rho, T (&J)[3]) {
+// rho1 and J1 at cell (x, y, z) at the current time (in stored units): the
+// pull-sum of the stored post-collision populations (Eq. 62 applied after the
+// advection of Eq. 64).
+template <typename S>
+__device__ __forceinline__ void pulled_moments(const Geometry &g, const S *__restrict__ src, int x, int y,
+                                               int z, typename Store<S>::R &rho,
+                                               typename Store<S>::R (&J)[3]) {
+    using R = typename Store<S>::R;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const long long nc = g.ncell;
     const long long id = ((long long)z * ny + y) * nx + x;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    const T f0 = src[id];
-    const T fpx = src[nc + id - x + xm];
-    const T fmx = src[2 * nc + id - x + xp];
-    const T fpy = src[3 * nc + ((long long)z * ny + ym) * nx + x];
-    const T fmy = src[4 * nc + ((long long)z * ny + yp) * nx + x];
+    const R f0 = Store<S>::get(src + id);
+    const R fpx = Store<S>::get(src + nc + id - x + xm);
+    const R fmx = Store<S>::get(src + 2 * nc + id - x + xp);
+    const R fpy = Store<S>::get(src + 3 * nc + ((long long)z * ny + ym) * nx + x);
+    const R fmy = Store<S>::get(src + 4 * nc + ((long long)z * ny + yp) * nx + x);
     rho = f0 + fpx + fmx + fpy + fmy;
     J[0] = fpx - fmx;
     J[1] = fpy - fmy;
-    J[2] = T(0);
+    J[2] = R(0);
     if (g.dim == 3) {
         const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-        const T fpz = src[5 * nc + ((long long)zm * ny + y) * nx + x];
-        const T fmz = src[6 * nc + ((long long)zp * ny + y) * nx + x];
+        const R fpz = Store<S>::get(src + 5 * nc + ((long long)zm * ny + y) * nx + x);
+        const R fmz = Store<S>::get(src + 6 * nc + ((long long)zp * ny + y) * nx + x);
         rho += fpz + fmz;
         J[2] = fpz - fmz;
     }
@@ -204,22 +261,24 @@ __device__ __forceinline__ void pulled_moments(const Geometry &g, const T *__res
 
 // One warp per surface element; lane l < 3^dim handles stencil cell l.
 // P = sum_l delta_l c_l^2 rho1_l and U = sum_l delta_l J1_l / rho0 (Eqs. 80-81),
-// then acc += (P^2, U.U, U_x (U.n), U_y (U.n), U_z (U.n)).
-template <typename T>
-__global__ void __launch_bounds__(256) sample_points(Geometry g, const T *__restrict__ src,
+// then acc += (P^2, U.U, U_x (U.n), U_y (U.n), U_z (U.n)) in stored units.
+template <typename S>
+__global__ void __launch_bounds__(256) sample_points(Geometry g, const S *__restrict__ src,
                                                      const int4 *__restrict__ st_xyz,
-                                                     const T *__restrict__ st_w,
-                                                     const T *__restrict__ nrm, T *__restrict__ acc) {
+                                                     const typename Store<S>::R *__restrict__ st_w,
+                                                     const typename Store<S>::R *__restrict__ nrm,
+                                                     typename Store<S>::R *__restrict__ acc) {
+    using R = typename Store<S>::R;
     const int lane = threadIdx.x & 31;
     const int k = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (k >= g.n_surface) return;  // uniform per warp
-    T p = T(0), u[3] = {T(0), T(0), T(0)};
+    R p = R(0), u[3] = {R(0), R(0), R(0)};
     if (lane < g.stencil) {
         const long long o = (long long)k * g.stencil + lane;
         const int4 c = st_xyz[o];
-        T rho, J[3];
+        R rho, J[3];
         pulled_moments(g, src, c.x, c.y, c.z, rho, J);
-        const T wp = st_w[2 * o], wu = st_w[2 * o + 1];
+        const R wp = st_w[2 * o], wu = st_w[2 * o + 1];
         p = wp * rho;
         u[0] = wu * J[0];
         u[1] = wu * J[1];
@@ -233,9 +292,9 @@ __global__ void __launch_bounds__(256) sample_points(Geometry g, const T *__rest
         u[2] += __shfl_xor_sync(kFull, u[2], m);
     }
     if (lane == 0) {
-        const T nx = nrm[4 * k], ny = nrm[4 * k + 1], nz = nrm[4 * k + 2];
-        const T un = u[0] * nx + u[1] * ny + u[2] * nz;
-        T *a = acc + 5 * (long long)k;
+        const R nx = nrm[4 * k], ny = nrm[4 * k + 1], nz = nrm[4 * k + 2];
+        const R un = u[0] * nx + u[1] * ny + u[2] * nz;
+        R *a = acc + 5 * (long long)k;
         a[0] += p * p;
         a[1] += u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         a[2] += u[0] * un;
@@ -244,13 +303,15 @@ __global__ void __launch_bounds__(256) sample_points(Geometry g, const T *__rest
     }
 }
 
-template <typename T>
-__global__ void fold_sums(int n, T *__restrict__ acc, double *__restrict__ acc64, int *__restrict__ err) {
+// acc64 += acc * scale (scale = 1 / pop_scale^2 converts stored units back).
+template <typename R>
+__global__ void fold_sums(int n, R *__restrict__ acc, double *__restrict__ acc64, double scale,
+                          int *__restrict__ err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double v = acc64[i] + (double)acc[i];
+    const double v = acc64[i] + (double)acc[i] * scale;
     acc64[i] = v;
-    acc[i] = T(0);
+    acc[i] = R(0);
     if (!isfinite(v)) atomicExch(err, 1);
 }
 
@@ -286,10 +347,11 @@ __global__ void __launch_bounds__(256) surface_force(Geometry g, const double *_
     }
 }
 
-template <typename T>
-__global__ void read_fields(Geometry g, const T *__restrict__ src, const uint8_t *__restrict__ cls,
-                            const T *__restrict__ c2f, long long first, long long count,
+template <typename S>
+__global__ void read_fields(Geometry g, const S *__restrict__ src, const uint8_t *__restrict__ cls,
+                            const typename Store<S>::R *__restrict__ c2f, long long first, long long count,
                             double *__restrict__ stage) {
+    using R = typename Store<S>::R;
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= count) return;
     const long long id = first + j;
@@ -297,90 +359,118 @@ __global__ void read_fields(Geometry g, const T *__restrict__ src, const uint8_t
     const long long r = id / g.n[0];
     const int y = (int)(r % g.n[1]);
     const int z = (int)(r / g.n[1]);
-    T rho, J[3];
+    R rho, J[3];
     pulled_moments(g, src, x, y, z, rho, J);
     const uint8_t k = cls[id];
-    const double c2 = k == CELL_FLUID ? (double)(T)(g.c0 * g.c0)
-                                      : (k == CELL_OBJECT ? (double)(T)(g.cp * g.cp) : (double)c2f[id]);
-    stage[j] = c2 * (double)rho;
-    for (int a = 0; a < g.dim; ++a) stage[(long long)(1 + a) * count + j] = (double)J[a] / g.rho0;
+    const double c2 = k == CELL_FLUID ? (double)(R)(g.c0 * g.c0)
+                                      : (k == CELL_OBJECT ? (double)(R)(g.cp * g.cp) : (double)c2f[id]);
+    const double unscale = 1.0 / g.pop_scale;
+    stage[j] = c2 * (double)rho * unscale;
+    for (int a = 0; a < g.dim; ++a) stage[(long long)(1 + a) * count + j] = (double)J[a] * unscale / g.rho0;
 }
 
-template <typename T, int D, int CH>
+template <typename S, int D, int CH>
 cudaError_t run_rows(const Geometry &g, const Buffers &b, int src, cudaStream_t s) {
+    using R = typename Store<S>::R;
     const long long rows = (long long)g.n[1] * g.n[2];
     const long long blocks = (rows * 32 + 255) / 256;
-    update_rows<T, D, CH><<<(unsigned)blocks, 256, 0, s>>>(
-        (const T *)b.pop[src], (T *)b.pop[src ^ 1], b.cls, (const T *)b.c2, g.n[0], g.n[1], g.n[2],
-        g.ncell, (T)(g.c0 * g.c0), (T)(g.cp * g.cp));
+    update_rows<S, D, CH><<<(unsigned)blocks, 256, 0, s>>>(
+        (const S *)b.pop[src], (S *)b.pop[src ^ 1], b.cls, (const R *)b.c2, g.n[0], g.n[1], g.n[2],
+        g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp));
     return cudaGetLastError();
 }
 
-template <typename T, int D>
+template <typename S>
+int row_chunks(const Geometry &g) {
+    constexpr int W = Store<S>::W;
+    if (g.n[0] % (32 * W) != 0) return 0;
+    const int ch = g.n[0] / (32 * W);
+    return ch <= 4 ? ch : 0;
+}
+
+template <typename S, int D>
 cudaError_t run_update(const Geometry &g, const Buffers &b, int src, cudaStream_t s, bool *vec) {
-    constexpr int W = 16 / sizeof(T);
-    const int nx = g.n[0];
-    if (nx % (32 * W) == 0) {
-        const int ch = nx / (32 * W);
-        *vec = true;
-        switch (ch) {
-            case 1: return run_rows<T, D, 1>(g, b, src, s);
-            case 2: return run_rows<T, D, 2>(g, b, src, s);
-            case 3: return run_rows<T, D, 3>(g, b, src, s);
-            case 4: return run_rows<T, D, 4>(g, b, src, s);
-            default: break;
-        }
+    using R = typename Store<S>::R;
+    const int ch = row_chunks<S>(g);
+    *vec = ch > 0;
+    switch (ch) {
+        case 1: return run_rows<S, D, 1>(g, b, src, s);
+        case 2: return run_rows<S, D, 2>(g, b, src, s);
+        case 3: return run_rows<S, D, 3>(g, b, src, s);
+        case 4: return run_rows<S, D, 4>(g, b, src, s);
+        default: break;
     }
-    *vec = false;
     const long long blocks = (g.ncell + 255) / 256;
-    update_cells<T, D><<<(unsigned)blocks, 256, 0, s>>>(
-        (const T *)b.pop[src], (T *)b.pop[src ^ 1], b.cls, (const T *)b.c2, g.n[0], g.n[1], g.n[2],
-        g.ncell, (T)(g.c0 * g.c0), (T)(g.cp * g.cp));
+    update_cells<S, D><<<(unsigned)blocks, 256, 0, s>>>(
+        (const S *)b.pop[src], (S *)b.pop[src ^ 1], b.cls, (const R *)b.c2, g.n[0], g.n[1], g.n[2],
+        g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp));
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t update_for(const Geometry &g, const Buffers &b, int src, cudaStream_t s, bool *vec) {
+    return g.dim == 3 ? run_update<S, 3>(g, b, src, s, vec) : run_update<S, 2>(g, b, src, s, vec);
+}
+
+template <typename S>
+cudaError_t sample_for(const Geometry &g, const Buffers &b, int src, cudaStream_t s) {
+    using R = typename Store<S>::R;
+    const unsigned blocks = (unsigned)((g.n_surface + 7) / 8);
+    sample_points<S><<<blocks, 256, 0, s>>>(g, (const S *)b.pop[src], b.st_xyz, (const R *)b.st_w,
+                                            (const R *)b.nrm, (R *)b.acc);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t fields_for(const Geometry &g, const Buffers &b, int src, long long first, long long count,
+                       cudaStream_t s) {
+    using R = typename Store<S>::R;
+    const unsigned blocks = (unsigned)((count + 255) / 256);
+    read_fields<S><<<blocks, 256, 0, s>>>(g, (const S *)b.pop[src], b.cls, (const R *)b.c2, first, count,
+                                          b.stage);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool update_is_vectorised(const Geometry &g, bool f64) {
-    const int W = f64 ? 2 : 4;
-    if (g.n[0] % (32 * W) != 0) return false;
-    const int ch = g.n[0] / (32 * W);
-    return ch >= 1 && ch <= 4;
+bool update_is_vectorised(const Geometry &g, Prec p) {
+    switch (p) {
+        case Prec::F64: return row_chunks<double>(g) > 0;
+        case Prec::F16: return row_chunks<__half>(g) > 0;
+        default: return row_chunks<float>(g) > 0;
+    }
 }
 
-cudaError_t launch_update(const Geometry &g, const Buffers &b, bool f64, int src, cudaStream_t s,
+cudaError_t launch_update(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s,
                           bool *vector_path) {
     bool vec = false;
     cudaError_t e;
-    if (f64)
-        e = g.dim == 3 ? run_update<double, 3>(g, b, src, s, &vec) : run_update<double, 2>(g, b, src, s, &vec);
-    else
-        e = g.dim == 3 ? run_update<float, 3>(g, b, src, s, &vec) : run_update<float, 2>(g, b, src, s, &vec);
+    switch (p) {
+        case Prec::F64: e = update_for<double>(g, b, src, s, &vec); break;
+        case Prec::F16: e = update_for<__half>(g, b, src, s, &vec); break;
+        default: e = update_for<float>(g, b, src, s, &vec); break;
+    }
     if (vector_path) *vector_path = vec;
     return e;
 }
 
-cudaError_t launch_sample(const Geometry &g, const Buffers &b, bool f64, int src, cudaStream_t s) {
+cudaError_t launch_sample(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s) {
     if (g.n_surface == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((g.n_surface + 7) / 8);
-    if (f64)
-        sample_points<double><<<blocks, 256, 0, s>>>(g, (const double *)b.pop[src], b.st_xyz,
-                                                     (const double *)b.st_w, (const double *)b.nrm,
-                                                     (double *)b.acc);
-    else
-        sample_points<float><<<blocks, 256, 0, s>>>(g, (const float *)b.pop[src], b.st_xyz,
-                                                    (const float *)b.st_w, (const float *)b.nrm,
-                                                    (float *)b.acc);
-    return cudaGetLastError();
+    switch (p) {
+        case Prec::F64: return sample_for<double>(g, b, src, s);
+        case Prec::F16: return sample_for<__half>(g, b, src, s);
+        default: return sample_for<float>(g, b, src, s);
+    }
 }
 
-cudaError_t launch_fold(const Geometry &g, const Buffers &b, bool f64, cudaStream_t s) {
+cudaError_t launch_fold(const Geometry &g, const Buffers &b, Prec p, cudaStream_t s) {
     if (g.n_surface == 0) return cudaSuccess;
     const int n = 5 * g.n_surface;
-    if (f64)
-        fold_sums<double><<<(n + 255) / 256, 256, 0, s>>>(n, (double *)b.acc, b.acc64, b.err);
+    const double scale = 1.0 / (g.pop_scale * g.pop_scale);
+    if (p == Prec::F64)
+        fold_sums<double><<<(n + 255) / 256, 256, 0, s>>>(n, (double *)b.acc, b.acc64, scale, b.err);
     else
-        fold_sums<float><<<(n + 255) / 256, 256, 0, s>>>(n, (float *)b.acc, b.acc64, b.err);
+        fold_sums<float><<<(n + 255) / 256, 256, 0, s>>>(n, (float *)b.acc, b.acc64, scale, b.err);
     return cudaGetLastError();
 }
 
@@ -389,16 +479,13 @@ cudaError_t launch_force(const Geometry &g, const Buffers &b, double n_window, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_fields(const Geometry &g, const Buffers &b, bool f64, int src, long long first,
+cudaError_t launch_fields(const Geometry &g, const Buffers &b, Prec p, int src, long long first,
                           long long count, cudaStream_t s) {
-    const unsigned blocks = (unsigned)((count + 255) / 256);
-    if (f64)
-        read_fields<double><<<blocks, 256, 0, s>>>(g, (const double *)b.pop[src], b.cls,
-                                                   (const double *)b.c2, first, count, b.stage);
-    else
-        read_fields<float><<<blocks, 256, 0, s>>>(g, (const float *)b.pop[src], b.cls,
-                                                  (const float *)b.c2, first, count, b.stage);
-    return cudaGetLastError();
+    switch (p) {
+        case Prec::F64: return fields_for<double>(g, b, src, first, count, s);
+        case Prec::F16: return fields_for<__half>(g, b, src, first, count, s);
+        default: return fields_for<float>(g, b, src, first, count, s);
+    }
 }
 
 }  // namespace wlb
