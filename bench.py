@@ -309,6 +309,78 @@ def run_gpu(args, prob):
         torch.distributed.destroy_process_group()
 
 
+def run_ensemble(args):
+    """Batched ensemble: forces/s of one batched launch sequence over all
+    lattices, against the same lattices run one at a time through the
+    single-lattice path (a sample of them, timed on the same GPU)."""
+    import torch
+
+    import paper_2404_02346_gb300 as wlb
+    from paper_2404_02346_gb300 import build as B
+
+    B.build()
+    if args.workload == "ensemble3d":
+        probs = workloads.ensemble_3d(seed=args.seed, precision=args.precision)
+        desc = "64 x 3D D3Q7 lattices, edge U{96,128,160}, lambda=edge/2, R~U[4,12], 1000 points, 25 periods"
+    else:
+        probs = workloads.ensemble_2d(seed=args.seed, precision=args.precision)
+        desc = "512 x 2D D2Q5 192^2 lattices, lambda=96, R~U[4,12], 1000 points, 25 periods"
+    stream = torch.cuda.Stream()
+    batch = wlb.Batch(probs, stream=stream)
+    tune = batch.autotune(steps_per_trial=16)
+    info = batch.info()
+    for _ in range(args.warmup):
+        F = batch.run()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    start.record(stream)
+    for _ in range(args.steps):
+        F = batch.run()
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end) / args.steps
+    batch.close()
+    # the same lattices through the single-lattice path, one after another
+    n_single = min(len(probs), 16 if args.workload == "ensemble3d" else 32)
+    idx = list(range(0, len(probs), max(1, len(probs) // n_single)))[:n_single]
+    singles, lu_single = [], 0
+    solvers = [wlb.Solver(probs[i], stream=stream) for i in idx]
+    solvers[0].run()  # graph capture outside the timed region
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in solvers:
+        singles.append(s.run())
+        lu_single += s.cells * s.info().n_steps
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = t0.elapsed_time(t1)
+    for s in solvers:
+        s.close()
+    ax = probs[0]["wave_axis"]
+    rel = max(abs(F[i, ax] - singles[k][ax]) / max(abs(singles[k][ax]), 1e-300) for k, i in enumerate(idx))
+    line = {
+        "metric": "radiation forces/s, batched ensemble", "value": len(probs) / (ms * 1e-3), "unit": "forces/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": desc, "lattices": len(probs), "lattice_updates": info.lattice_updates,
+                   "tuning": tune, "l2": "inputs larger than L2"},
+        "glups": info.lattice_updates / (ms * 1e-3) / 1e9,
+        "single_instance": {"forces_per_s": len(idx) / (ms_single * 1e-3), "sampled_lattices": len(idx),
+                            "glups": lu_single / (ms_single * 1e-3) / 1e9,
+                            "max_rel_force_diff_vs_batch": rel},
+        "speedup_vs_single": (len(probs) / (ms * 1e-3)) / (len(idx) / (ms_single * 1e-3)),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_profile(args, prob):
     """A short pass over the benchmark lattice for ncu: setup, 64 unsampled and
     64 sampled steps (graph-replayed where whole periods allow), the force."""
@@ -340,10 +412,14 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=64)
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"],
                     help="population storage (the benchmark workload is FP32)")
+    ap.add_argument("--workload", default="sphere256", choices=["sphere256", "ensemble3d", "ensemble2d"],
+                    help="sphere256: the benchmark line; ensembles: batched forces/s")
     args = ap.parse_args()
     prob = workloads.sphere_3d(seed=args.seed, precision=args.precision)
     if args.profile:
         run_profile(args, prob)
+    elif args.workload != "sphere256":
+        run_ensemble(args)
     elif args.impl == "reference":
         run_reference(args, prob)
     else:

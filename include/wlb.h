@@ -212,6 +212,57 @@ wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out);
 #define WLB_NOALLOC_MAX_SURFACE 8192
 wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, double force_out[3]);
 
+/*
+ * Batched ensembles (Secs. V-VII protocol, run for many independent problems).
+ *
+ * count lattices of uneven size, one parameter set each (same lattice type and
+ * precision; nx a multiple of 16 bytes of populations and at most 512 FP32 /
+ * 256 FP64 / 1024 FP16 cells), stepped together: one launch per step updates
+ * every row of every lattice still running, one launch samples every surface
+ * point of every lattice inside its averaging window, and the step index lives
+ * in device memory, so chunks of 64 steps replay as one CUDA graph.  Each
+ * lattice follows exactly the protocol of wlb_run (its own period, n_periods
+ * and n_avg_periods; a lattice stops at its own last step).
+ *
+ *   wlb_batch_workspace_bytes  device bytes for the batch (per-lattice regions
+ *                              as in wlb_workspace_bytes, plus tables).
+ *   wlb_batch_create           ws: NULL (library cudaMalloc) or a 256-byte
+ *                              aligned device pointer of at least that size;
+ *                              stream: cudaStream_t for all work.
+ *   wlb_batch_autotune         times every launch shape (threads per block in
+ *                              {128, 256} x blocks per SM in {2, 4, 8, 16}) for
+ *                              steps_per_trial steps from a fresh setup and keeps
+ *                              the fastest; the chosen shape is returned in
+ *                              *best (may be NULL).  Leaves the lattices in an
+ *                              advanced state; wlb_batch_run starts from setup.
+ *   wlb_batch_run              setup, all steps, forces: forces_out is count x 3
+ *                              host doubles (lattice order).  Synchronises.
+ *                              WLB_ERR_UNSTABLE if any lattice's sums are not
+ *                              finite.
+ * WLB_ERR_ARG for count < 1, an invalid parameter set, mixed lattice types or
+ * precisions, or a row length the batched update does not cover.
+ */
+typedef struct wlb_batch wlb_batch;
+typedef struct {
+    int threads_per_block, blocks_per_sm;
+    float ms_per_step;
+} wlb_batch_tuning;
+typedef struct {
+    int count;
+    long long total_rows, total_points, max_steps;
+    long long lattice_updates;      /* sum over lattices of cells x steps */
+    int threads_per_block, blocks_per_sm, row_chunks;
+} wlb_batch_info;
+
+wlb_status wlb_batch_workspace_bytes(const wlb_params *ps, int count, size_t *bytes);
+wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws_bytes, void *stream,
+                            wlb_batch **out);
+wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tuning *best);
+wlb_status wlb_batch_run(wlb_batch *b, double *forces_out);
+wlb_status wlb_batch_get_info(const wlb_batch *b, wlb_batch_info *out);
+const char *wlb_batch_last_error(const wlb_batch *b);
+wlb_status wlb_batch_destroy(wlb_batch *b);
+
 /* Sizes and counters of a handle. */
 wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
 

@@ -55,6 +55,20 @@ class Info(ctypes.Structure):
     ]
 
 
+class BatchTuning(ctypes.Structure):
+    """Mirror of ``wlb_batch_tuning``."""
+    _fields_ = [("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("ms_per_step", ctypes.c_float)]
+
+
+class BatchInfo(ctypes.Structure):
+    """Mirror of ``wlb_batch_info``."""
+    _fields_ = [("count", ctypes.c_int), ("total_rows", ctypes.c_longlong),
+                ("total_points", ctypes.c_longlong), ("max_steps", ctypes.c_longlong),
+                ("lattice_updates", ctypes.c_longlong), ("threads_per_block", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("row_chunks", ctypes.c_int)]
+
+
 _lib = None
 # Functions declared in include/wlb.h, with their ctypes signatures.
 _VP = ctypes.c_void_p
@@ -73,6 +87,15 @@ _SIGNATURES = {
     "wlb_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(Info)]),
     "wlb_destroy": (ctypes.c_int, [_VP]),
     "wlb_average_noalloc": (ctypes.c_int, [_VP, ctypes.c_longlong, _DP]),
+    "wlb_batch_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "wlb_batch_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, _VP, ctypes.c_size_t, _VP,
+                                        ctypes.POINTER(_VP)]),
+    "wlb_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(BatchTuning)]),
+    "wlb_batch_run": (ctypes.c_int, [_VP, _DP]),
+    "wlb_batch_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(BatchInfo)]),
+    "wlb_batch_last_error": (ctypes.c_char_p, [_VP]),
+    "wlb_batch_destroy": (ctypes.c_int, [_VP]),
     "wlb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "wlb_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -223,3 +246,68 @@ def compute_force(problem, precision=None):
     """One force evaluation through the public API (host in, host out)."""
     with Solver(problem, precision=precision) as s:
         return s.run()
+
+
+class Batch:
+    """Many independent lattices (same lattice type and precision) stepped
+    together by the batched kernels (wlb_batch_*).  One torch workspace."""
+
+    def __init__(self, problems, stream=None, precision=None):
+        import torch
+
+        self.problems = list(problems)
+        n = len(self.problems)
+        arr = (Params * n)(*[params_from_problem(p, precision) for p in self.problems])
+        self._params = arr
+        L = lib()
+        nb = ctypes.c_size_t()
+        _check(L.wlb_batch_workspace_bytes(arr, n, ctypes.byref(nb)), what="wlb_batch_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ws = torch.empty(nb.value, dtype=torch.uint8, device=self.stream.device)
+        h = _VP()
+        _check(L.wlb_batch_create(arr, n, ctypes.c_void_p(self._ws.data_ptr()), nb.value,
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+               what="wlb_batch_create")
+        self._h = h
+        self.count = n
+
+    def _bcheck(self, status, what):
+        if status != WLB_OK:
+            L = lib()
+            raise WlbError(status, "%s: %s %s" % (what, L.wlb_status_str(status).decode(),
+                                                   L.wlb_batch_last_error(self._h).decode()))
+
+    def info(self):
+        out = BatchInfo()
+        self._bcheck(lib().wlb_batch_get_info(self._h, ctypes.byref(out)), "wlb_batch_get_info")
+        return out
+
+    def autotune(self, steps_per_trial=16):
+        t = BatchTuning()
+        self._bcheck(lib().wlb_batch_autotune(self._h, int(steps_per_trial), ctypes.byref(t)),
+                     "wlb_batch_autotune")
+        return {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm,
+                "ms_per_step": t.ms_per_step}
+
+    def run(self):
+        F = np.zeros((self.count, 3))
+        self._bcheck(lib().wlb_batch_run(self._h, F.ctypes.data_as(_DP)), "wlb_batch_run")
+        return F
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wlb_batch_destroy(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -47,6 +47,10 @@ int dim_of(const wlb_params *p) { return p->lattice == WLB_D2Q5 ? 2 : 3; }
 
 bool whole(double v) { return std::isfinite(v) && v > 0 && std::fabs(v - std::nearbyint(v)) < 1e-9 * std::fmax(1.0, v); }
 
+}  // namespace
+
+namespace wlb {
+
 Geometry make_geometry(const wlb_params *p) {
     Geometry g{};
     g.dim = dim_of(p);
@@ -75,13 +79,13 @@ Geometry make_geometry(const wlb_params *p) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-wlb::Prec prec_of(const wlb_params *p) {
+Prec prec_of(const wlb_params *p) {
     return p->precision == WLB_POP_F64 ? wlb::Prec::F64
                                        : (p->precision == WLB_POP_F16 ? wlb::Prec::F16 : wlb::Prec::F32);
 }
 
 // Carve the workspace; with base == nullptr only the size is computed.
-size_t layout(const Geometry &g, wlb::Prec prec, char *base, Buffers *b) {
+size_t layout(const Geometry &g, Prec prec, char *base, Buffers *b) {
     const size_t P = wlb::pop_bytes(prec), T = wlb::real_bytes(prec);
     const size_t nc = (size_t)g.ncell, N = (size_t)g.n_surface, S = (size_t)g.stencil;
     size_t off = 0;
@@ -108,6 +112,14 @@ size_t layout(const Geometry &g, wlb::Prec prec, char *base, Buffers *b) {
     if (b) *b = t;
     return off;
 }
+
+}  // namespace wlb
+
+namespace {
+
+using wlb::layout;
+using wlb::make_geometry;
+using wlb::prec_of;
 
 void destroy_graphs(wlb_handle *h) {
     for (int i = 0; i < 2; ++i) {

@@ -3,6 +3,13 @@
 #include "../../include/wlb.h"
 #include "wlb_internal.cuh"
 
+namespace wlb {
+// Host helpers of the C ABI (wlb_api.cu).
+Geometry make_geometry(const wlb_params *p);
+Prec prec_of(const wlb_params *p);
+size_t layout(const Geometry &g, Prec prec, char *base, Buffers *b);  // size only if base == nullptr
+}  // namespace wlb
+
 struct wlb_handle {
     wlb_params p;
     wlb::Geometry g;

@@ -1,0 +1,111 @@
+// Device-side building blocks shared by the single-lattice and batched kernels:
+// storage traits of the populations and the pull-sum of the moments.
+#pragma once
+#include <cuda_fp16.h>
+
+#include "wlb_internal.cuh"
+
+namespace wlb {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Storage traits: R is the arithmetic type, W the values per 16-byte vector.
+// Vector accesses use streaming cache hints: every population is read once and
+// written once per step.
+template <typename S> struct Store;
+
+template <> struct Store<float> {
+    using R = float;
+    static constexpr int W = 4;
+    __device__ static void load(const float *p, float (&v)[4]) {
+        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ static void store(float *p, const float (&v)[4]) {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
+    __device__ static float get(const float *p) { return *p; }
+    __device__ static void put(float *p, float v) { *p = v; }
+};
+
+template <> struct Store<double> {
+    using R = double;
+    static constexpr int W = 2;
+    __device__ static void load(const double *p, double (&v)[2]) {
+        const double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    }
+    __device__ static void store(double *p, const double (&v)[2]) {
+        __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+    }
+    __device__ static double get(const double *p) { return *p; }
+    __device__ static void put(double *p, double v) { *p = v; }
+};
+
+template <> struct Store<__half> {
+    using R = float;
+    static constexpr int W = 8;
+    __device__ static void load(const __half *p, float (&v)[8]) {
+        const uint4 t = __ldcs(reinterpret_cast<const uint4 *>(p));
+        const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h;
+            memcpy(&h, &w[i], 4);
+            const float2 f = __half22float2(h);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    }
+    __device__ static void store(__half *p, const float (&v)[8]) {
+        unsigned w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+            memcpy(&w[i], &h, 4);
+        }
+        __stcs(reinterpret_cast<uint4 *>(p), make_uint4(w[0], w[1], w[2], w[3]));
+    }
+    __device__ static float get(const __half *p) { return __half2float(*p); }
+    __device__ static void put(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
+template <int W>
+__device__ __forceinline__ unsigned long long load_classes(const uint8_t *p) {
+    if constexpr (W == 8) return *reinterpret_cast<const unsigned long long *>(p);
+    else if constexpr (W == 4) return *reinterpret_cast<const uint32_t *>(p);
+    else return *reinterpret_cast<const uint16_t *>(p);
+}
+
+// rho1 and J1 at cell (x, y, z) at the current time (in stored units): the
+// pull-sum of the stored post-collision populations (Eq. 62 applied after the
+// advection of Eq. 64).
+template <typename S>
+__device__ __forceinline__ void pulled_moments(const Geometry &g, const S *__restrict__ src, int x, int y,
+                                               int z, typename Store<S>::R &rho,
+                                               typename Store<S>::R (&J)[3]) {
+    using R = typename Store<S>::R;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long nc = g.ncell;
+    const long long id = ((long long)z * ny + y) * nx + x;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const R f0 = Store<S>::get(src + id);
+    const R fpx = Store<S>::get(src + nc + id - x + xm);
+    const R fmx = Store<S>::get(src + 2 * nc + id - x + xp);
+    const R fpy = Store<S>::get(src + 3 * nc + ((long long)z * ny + ym) * nx + x);
+    const R fmy = Store<S>::get(src + 4 * nc + ((long long)z * ny + yp) * nx + x);
+    rho = f0 + fpx + fmx + fpy + fmy;
+    J[0] = fpx - fmx;
+    J[1] = fpy - fmy;
+    J[2] = R(0);
+    if (g.dim == 3) {
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        const R fpz = Store<S>::get(src + 5 * nc + ((long long)zm * ny + y) * nx + x);
+        const R fmz = Store<S>::get(src + 6 * nc + ((long long)zp * ny + y) * nx + x);
+        rho += fpz + fmz;
+        J[2] = fpz - fmz;
+    }
+}
+
+}  // namespace wlb

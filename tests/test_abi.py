@@ -108,3 +108,26 @@ def test_null_arguments(wlb):
     assert L.wlb_step(None, 1, 0) == wlb.WLB_ERR_ARG
     assert L.wlb_destroy(None) == wlb.WLB_ERR_ARG
     assert L.wlb_last_error(None) == b""
+
+
+def test_batch_workspace_validation(wlb):
+    """wlb_batch_workspace_bytes checks the batch on the host: mixed lattice
+    types or precisions and rows the batched update does not cover are rejected."""
+    L = wlb.lib()
+    a = _valid()
+    b = workloads.problem(2, (48, 32), 1, 16.0, 3.0, (24.0, 2.0), cp=0.3, n_surface=8,
+                          n_periods=2, n_avg_periods=1)
+    nb = ctypes.c_size_t()
+
+    def arr(*probs):
+        return (wlb.Params * len(probs))(*[wlb.params_from_problem(p) for p in probs])
+
+    assert L.wlb_batch_workspace_bytes(arr(a, a), 2, ctypes.byref(nb)) == wlb.WLB_OK
+    single = wlb.workspace_bytes(wlb.params_from_problem(a))
+    assert nb.value >= 2 * single
+    assert L.wlb_batch_workspace_bytes(arr(a, b), 2, ctypes.byref(nb)) == wlb.WLB_ERR_ARG
+    assert L.wlb_batch_workspace_bytes(arr(a, dict(a, precision="f64")), 2, ctypes.byref(nb)) == wlb.WLB_ERR_ARG
+    wide = workloads.problem(2, (1024, 32), 1, 16.0, 3.0, (512.0, 2.0), cp=0.3, n_surface=8,
+                             n_periods=2, n_avg_periods=1)
+    assert L.wlb_batch_workspace_bytes(arr(wide), 1, ctypes.byref(nb)) == wlb.WLB_ERR_ARG
+    assert L.wlb_batch_workspace_bytes(arr(a), 0, ctypes.byref(nb)) == wlb.WLB_ERR_ARG

@@ -1,0 +1,99 @@
+"""Batched ensembles (wlb_batch_*) against single-lattice runs and the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wlb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2404_02346_gb300 import build as B
+    B.build()
+    import paper_2404_02346_gb300 as W
+    W.lib()
+    return W
+
+
+def _members_3d(precision="f32"):
+    # ragged rows (40, 96, 64, 160 cells): the widest needs two 128-cell chunks,
+    # so every row runs the two-chunk code with idle lanes; uneven periods and
+    # run lengths (the longest lattice keeps stepping after the others stop)
+    specs = [((40, 36, 32), 16.0, 4.0, 30, 10), ((96, 24, 32), 16.0, 3.0, 20, 5),
+             ((64, 24, 24), 24.0, 3.5, 12, 4), ((160, 24, 32), 32.0, 3.0, 6, 2)]
+    out = []
+    for i, (n, lam, R, per, avg) in enumerate(specs):
+        c = (n[0] / 2 + 0.25, n[1] / 2 - 0.5, lam / 8 + 0.125 * i)
+        out.append(workloads.problem(3, n, 2, lam, R, c, cp=0.25 * (0.8 + 0.3 * i), n_surface=100 + 50 * i,
+                                     n_periods=per, n_avg_periods=avg, precision=precision))
+    return out
+
+
+def test_batch_3d_matches_single_and_oracle(wlb):
+    probs = _members_3d()
+    with wlb.Batch(probs) as b:
+        info = b.info()
+        assert info.count == 4 and info.row_chunks == 2
+        F = b.run()
+        F2 = b.run()  # a second run from a fresh setup gives the same forces
+    assert np.array_equal(F, F2)
+    for i, p in enumerate(probs):
+        with wlb.Solver(p) as s:
+            Fs = s.run()
+        ax = p["wave_axis"]
+        assert abs(F[i, ax] - Fs[ax]) <= 1e-6 * abs(Fs[ax]), (i, F[i], Fs)
+    o = oracle.run(probs[0])["force"]
+    assert abs(F[0, 2] - o[2]) <= 1e-3 * abs(o[2])
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64", "f16"])
+def test_batch_2d_ragged(wlb, precision):
+    specs = [((48, 32), 16.0, 3.0, 8), ((192, 96), 48.0, 6.0, 4), ((24, 64), 32.0, 4.0, 5)]
+    if precision == "f16":  # 16-byte rows of FP16 need nx % 8 == 0
+        specs[2] = ((32, 64), 32.0, 4.0, 5)
+    probs = [workloads.problem(2, n, 1, lam, R, (n[0] / 2 + 0.25, lam / 8), cp=0.32, n_surface=40,
+                               n_periods=per, n_avg_periods=2, precision=precision)
+             for (n, lam, R, per) in specs]
+    with wlb.Batch(probs) as b:
+        F = b.run()
+    # FP16: a one-ulp FP32 difference between kernels can flip one FP16 rounding
+    tol = {"f32": 1e-6, "f64": 1e-12, "f16": 1e-3}[precision]
+    for i, p in enumerate(probs):
+        with wlb.Solver(p) as s:
+            Fs = s.run()
+        assert abs(F[i, 1] - Fs[1]) <= tol * abs(Fs[1]), (i, F[i], Fs)
+
+
+def test_batch_autotune_and_member_without_window(wlb):
+    probs = _members_3d()
+    probs[1] = dict(probs[1], n_window=0)  # no averaging window: zero force, still stepped
+    with wlb.Batch(probs) as b:
+        best = b.autotune(steps_per_trial=8)
+        assert best["threads_per_block"] in (128, 256) and best["blocks_per_sm"] in (2, 4, 8, 16)
+        info = b.info()
+        assert info.threads_per_block == best["threads_per_block"]
+        F = b.run()
+    assert np.array_equal(F[1], np.zeros(3))
+    with wlb.Solver(probs[0]) as s:
+        Fs = s.run()
+    assert abs(F[0, 2] - Fs[2]) <= 1e-6 * abs(Fs[2])
+
+
+def test_batch_rejects_mixed_or_unsupported(wlb):
+    p3 = _members_3d()[0]
+    p2 = workloads.problem(2, (48, 32), 1, 16.0, 3.0, (24.0, 2.0), cp=0.3, n_surface=8,
+                           n_periods=2, n_avg_periods=1)
+    with pytest.raises(wlb.WlbError):
+        wlb.Batch([p3, p2])
+    with pytest.raises(wlb.WlbError):
+        wlb.Batch([p3, dict(p3, precision="f64")])
+    wide = workloads.problem(2, (1024, 32), 1, 16.0, 3.0, (512.0, 2.0), cp=0.3, n_surface=8,
+                             n_periods=2, n_avg_periods=1)  # 1024 FP32 cells > 4 chunks
+    with pytest.raises(wlb.WlbError):
+        wlb.Batch([wide])

@@ -114,3 +114,40 @@ def sphere_3d_large(position=0, n_periods=30, n_avg_periods=10, precision="f32")
     return sphere_3d(n=512, wavelength=lam, radius=24.0, n_surface=4096, kappa=0.5,
                      z0=z0, n_periods=n_periods, n_avg_periods=n_avg_periods,
                      precision=precision)
+
+
+def _ensemble_member(g, dim, edge, n_surface, n_periods, n_avg_periods, precision):
+    """One ensemble lattice: lambda = edge/2, R ~ U[4, 12], k z0 ~ U[0, pi],
+    sound-speed ratio c~ ~ U[0.8, 2.0] (density matched, so kappa~ = 1/c~^2)."""
+    lam = edge / 2.0
+    R = quantise(4.0 + 8.0 * g.uniform())
+    kz = math.pi * g.uniform()
+    c_ratio = 0.8 + 1.2 * g.uniform()
+    z0 = kz * lam / (2.0 * math.pi)
+    center = (edge / 2.0,) * (dim - 1) + (z0,)
+    n = (edge,) * dim
+    p = problem(dim, n, dim - 1, lam, R, center, cp=c_ratio * 0.25, n_surface=n_surface,
+                n_periods=n_periods, n_avg_periods=n_avg_periods, precision=precision)
+    p.update({"kz": kz, "c_ratio": c_ratio, "kappa": 1.0 / c_ratio ** 2,
+              "ka": 2.0 * math.pi / lam * R})
+    return p
+
+
+def ensemble_3d(seed=1, count=64, n_surface=1000, n_periods=25, n_avg_periods=10, precision="f32"):
+    """Batched ensemble: count independent 3D lattices with edge uniform in
+    {96, 128, 160}, lambda = edge/2, R ~ U[4, 12], k z0 ~ U[0, pi], c~ ~ U[0.8, 2.0],
+    1000 surface points, 25 periods (last 10 averaged)."""
+    g = SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        edge = (96, 128, 160)[min(2, int(3 * g.uniform()))]
+        out.append(_ensemble_member(g, 3, edge, n_surface, n_periods, n_avg_periods, precision))
+    return out
+
+
+def ensemble_2d(seed=1, count=512, edge=192, n_surface=1000, n_periods=25, n_avg_periods=10,
+                precision="f32"):
+    """2D variant: count cylinders on edge^2 lattices (192^2), lambda = edge/2."""
+    g = SplitMix64(seed)
+    return [_ensemble_member(g, 2, edge, n_surface, n_periods, n_avg_periods, precision)
+            for _ in range(count)]
