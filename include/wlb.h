@@ -49,7 +49,8 @@ typedef enum {
     WLB_ERR_UNSTABLE = 2,  /* non-finite time-average accumulators              */
     WLB_ERR_CUDA = 3,      /* a CUDA runtime call or kernel launch failed       */
     WLB_ERR_OOM = 4,       /* device or host allocation failed, or workspace too small */
-    WLB_ERR_STATE = 5      /* call out of order (e.g. wlb_step before wlb_init) */
+    WLB_ERR_STATE = 5,     /* call out of order (e.g. wlb_step before wlb_init) */
+    WLB_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up (reported, never a hang) */
 } wlb_status;
 
 typedef enum { WLB_D2Q5 = 0, WLB_D3Q7 = 1 } wlb_lattice;          /* Fig. 8   */
@@ -262,6 +263,53 @@ wlb_status wlb_batch_run(wlb_batch *b, double *forces_out);
 wlb_status wlb_batch_get_info(const wlb_batch *b, wlb_batch_info *out);
 const char *wlb_batch_last_error(const wlb_batch *b);
 wlb_status wlb_batch_destroy(wlb_batch *b);
+
+/*
+ * Learned surrogate of the force (not part of the paper's method; the lattice
+ * runs above generate its training data and judge its error).
+ *
+ * MLP 4 -> 256 -> 256 -> 256 -> 1, GELU(z) = z Phi(z) on the hidden layers,
+ * linear output, mean-squared-error loss.  Inputs are the four features
+ * (k R_p, k z0, kappa~ = kappa_p/kappa_0, c~ = c_p/c_0), normalised to [-1, 1]
+ * by the box [x_lo, x_hi] given at creation, which is also the "training hull"
+ * reported by wlb_mlp_predict.  Every matrix product runs on the tensor cores
+ * (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory); weights and
+ * activations are BF16, the Adam masters FP32.
+ *
+ * Packed parameter vector (FP32, wlb_mlp_param_count() values): W1 [256][4],
+ * b1 [256], W2 [256][256], b2, W3 [256][256], b3, W4 [1][256], b4 [1].
+ *
+ *   wlb_mlp_create       batch_max: multiple of 128 (<= 4 Mi); allocates its
+ *                        device buffers with cudaMalloc; weights all zero.
+ *   wlb_mlp_init_weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed).
+ *   wlb_mlp_set_weights / wlb_mlp_get_weights   host FP32 packed vector;
+ *                        set resets the Adam state.
+ *   wlb_mlp_loss_grad    x: device n x 4 FP32, t: device n FP32 (n <= batch_max);
+ *                        loss (host float, may be NULL) and gradient (host
+ *                        packed FP32, may be NULL); no update.
+ *   wlb_mlp_train        epochs over n device samples in shuffled whole
+ *                        batches (SplitMix64(seed) Fisher-Yates), Adam
+ *                        (0.9, 0.999, 1e-8) with the learning rate decayed
+ *                        geometrically from lr to lr_final; loss_history
+ *                        (host, epochs floats, may be NULL) gets each epoch's
+ *                        mean batch loss.
+ *   wlb_mlp_predict      x: device n x 4, y: device n FP32, inside: device n
+ *                        bytes (may be NULL): 1 if the query lies in the box.
+ * All calls synchronise the stream before returning.  WLB_ERR_TIMEOUT if a
+ * tensor-core completion wait gave up (the kernel returns instead of hanging).
+ */
+typedef struct wlb_mlp wlb_mlp;
+int wlb_mlp_param_count(void);
+wlb_status wlb_mlp_create(int batch_max, const float x_lo[4], const float x_hi[4], void *stream, wlb_mlp **out);
+wlb_status wlb_mlp_init_weights(wlb_mlp *m, unsigned long long seed);
+wlb_status wlb_mlp_set_weights(wlb_mlp *m, const float *w);
+wlb_status wlb_mlp_get_weights(wlb_mlp *m, float *w);
+wlb_status wlb_mlp_loss_grad(wlb_mlp *m, const float *x, const float *t, int n, float *loss, float *grad);
+wlb_status wlb_mlp_train(wlb_mlp *m, const float *x, const float *t, long long n, int epochs, int batch, float lr,
+                         float lr_final, unsigned long long seed, float *loss_history);
+wlb_status wlb_mlp_predict(wlb_mlp *m, const float *x, long long n, float *y, unsigned char *inside);
+const char *wlb_mlp_last_error(const wlb_mlp *m);
+wlb_status wlb_mlp_destroy(wlb_mlp *m);
 
 /* Sizes and counters of a handle. */
 wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libwlb.so")
 
-WLB_OK, WLB_ERR_ARG, WLB_ERR_UNSTABLE, WLB_ERR_CUDA, WLB_ERR_OOM, WLB_ERR_STATE = range(6)
+WLB_OK, WLB_ERR_ARG, WLB_ERR_UNSTABLE, WLB_ERR_CUDA, WLB_ERR_OOM, WLB_ERR_STATE, WLB_ERR_TIMEOUT = range(7)
 WLB_D2Q5, WLB_D3Q7 = 0, 1
 WLB_POP_F32, WLB_POP_F64, WLB_POP_F16 = 0, 1, 2
 
@@ -96,6 +96,19 @@ _SIGNATURES = {
     "wlb_batch_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(BatchInfo)]),
     "wlb_batch_last_error": (ctypes.c_char_p, [_VP]),
     "wlb_batch_destroy": (ctypes.c_int, [_VP]),
+    "wlb_mlp_param_count": (ctypes.c_int, []),
+    "wlb_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                      _VP, ctypes.POINTER(_VP)]),
+    "wlb_mlp_init_weights": (ctypes.c_int, [_VP, ctypes.c_ulonglong]),
+    "wlb_mlp_set_weights": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "wlb_mlp_get_weights": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "wlb_mlp_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                         ctypes.POINTER(ctypes.c_float)]),
+    "wlb_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)]),
+    "wlb_mlp_predict": (ctypes.c_int, [_VP, _VP, ctypes.c_longlong, _VP, _VP]),
+    "wlb_mlp_last_error": (ctypes.c_char_p, [_VP]),
+    "wlb_mlp_destroy": (ctypes.c_int, [_VP]),
     "wlb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "wlb_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -311,3 +324,78 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+_FP = ctypes.POINTER(ctypes.c_float)
+
+
+class MLP:
+    """The surrogate network (wlb_mlp_*).  Samples and outputs are torch CUDA
+    tensors (float32); weights and gradients come back as numpy float32."""
+
+    def __init__(self, x_lo, x_hi, batch_max=4096, stream=None):
+        import torch
+
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        lo = (ctypes.c_float * 4)(*[float(v) for v in x_lo])
+        hi = (ctypes.c_float * 4)(*[float(v) for v in x_hi])
+        h = _VP()
+        _check(lib().wlb_mlp_create(int(batch_max), lo, hi, ctypes.c_void_p(self.stream.cuda_stream),
+                                    ctypes.byref(h)), what="wlb_mlp_create")
+        self._h = h
+        self.n_params = lib().wlb_mlp_param_count()
+        self.batch_max = batch_max
+
+    def _mcheck(self, status, what):
+        if status != WLB_OK:
+            L = lib()
+            raise WlbError(status, "%s: %s %s" % (what, L.wlb_status_str(status).decode(),
+                                                   L.wlb_mlp_last_error(self._h).decode()))
+
+    def init_weights(self, seed):
+        self._mcheck(lib().wlb_mlp_init_weights(self._h, int(seed)), "wlb_mlp_init_weights")
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self._mcheck(lib().wlb_mlp_set_weights(self._h, w.ctypes.data_as(_FP)), "wlb_mlp_set_weights")
+
+    def get_weights(self):
+        w = np.zeros(self.n_params, dtype=np.float32)
+        self._mcheck(lib().wlb_mlp_get_weights(self._h, w.ctypes.data_as(_FP)), "wlb_mlp_get_weights")
+        return w
+
+    def loss_grad(self, x, t):
+        loss = ctypes.c_float()
+        g = np.zeros(self.n_params, dtype=np.float32)
+        self._mcheck(lib().wlb_mlp_loss_grad(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                             int(x.shape[0]), ctypes.byref(loss), g.ctypes.data_as(_FP)),
+                     "wlb_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, x, t, epochs, batch=512, lr=1e-3, lr_final=5e-5, seed=1):
+        hist = np.zeros(epochs, dtype=np.float32)
+        self._mcheck(lib().wlb_mlp_train(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                         int(x.shape[0]), int(epochs), int(batch), float(lr), float(lr_final),
+                                         int(seed), hist.ctypes.data_as(_FP)), "wlb_mlp_train")
+        return hist
+
+    def predict(self, x):
+        import torch
+
+        n = int(x.shape[0])
+        y = torch.empty(n, dtype=torch.float32, device=x.device)
+        inside = torch.empty(n, dtype=torch.uint8, device=x.device)
+        self._mcheck(lib().wlb_mlp_predict(self._h, ctypes.c_void_p(x.data_ptr()), n, ctypes.c_void_p(y.data_ptr()),
+                                           ctypes.c_void_p(inside.data_ptr())), "wlb_mlp_predict")
+        return y, inside
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wlb_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

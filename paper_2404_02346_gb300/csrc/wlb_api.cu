@@ -177,6 +177,7 @@ const char *wlb_status_str(wlb_status s) {
         case WLB_ERR_CUDA: return "CUDA error";
         case WLB_ERR_OOM: return "out of memory or workspace too small";
         case WLB_ERR_STATE: return "call out of order";
+        case WLB_ERR_TIMEOUT: return "device wait limit reached";
     }
     return "unknown status";
 }

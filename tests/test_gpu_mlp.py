@@ -1,0 +1,95 @@
+"""Surrogate network on the tensor cores (wlb_mlp_*) against the FP64 oracle
+network: forward values and backpropagated gradients for the same BF16-rounded
+weights and inputs, and training on a smooth target."""
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+LO = np.array([0.1, 0.0, 0.2, 0.8])
+HI = np.array([1.2, np.pi, 1.6, 2.0])
+
+
+@pytest.fixture(scope="module")
+def wlb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2404_02346_gb300 import build as B
+    B.build()
+    import paper_2404_02346_gb300 as W
+    W.lib()
+    return W
+
+
+def _inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    return LO + (HI - LO) * rng.uniform(size=(n, 4))
+
+
+def _bf16_theta(theta):
+    return ref.bf16(theta)
+
+
+def test_forward_matches_oracle(wlb):
+    import torch
+    net = wlb.MLP(LO, HI, batch_max=1024)
+    net.init_weights(11)
+    w = net.get_weights().astype(np.float64)
+    x = _inputs(1000, 1)  # 1000 queries: a ragged last tile of 128 rows
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    y, inside = net.predict(xt)
+    y = y.cpu().numpy().astype(np.float64)
+    assert inside.cpu().numpy().all()
+    xn = ref.bf16(ref.normalise(x.astype(np.float32).astype(np.float64), LO.astype(np.float32), HI.astype(np.float32)))
+    y_ref, _ = ref.forward(_bf16_theta(w), xn)
+    scale = np.abs(y_ref).max()
+    assert np.abs(y - y_ref).max() <= 2e-2 * scale, (np.abs(y - y_ref).max(), scale)
+    # outside the box: flagged
+    xo = x[:4].copy()
+    xo[0, 0] = 5.0
+    xo[1, 3] = 0.1
+    _, ins = net.predict(torch.tensor(xo, dtype=torch.float32, device="cuda"))
+    assert list(ins.cpu().numpy()) == [0, 0, 1, 1]
+    net.close()
+
+
+def test_gradients_match_oracle(wlb):
+    """Loss and gradients of a 384-sample batch (three 128-row tiles) against
+    FP64 backpropagation with the same BF16 weights and inputs; the GPU keeps
+    activations and activation gradients in BF16, hence the per-block bound."""
+    import torch
+    net = wlb.MLP(LO, HI, batch_max=512)
+    net.init_weights(5)
+    w = net.get_weights().astype(np.float64)
+    x = _inputs(384, 2)
+    rng = np.random.default_rng(3)
+    t = rng.standard_normal(384) * 0.5
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    tt = torch.tensor(t, dtype=torch.float32, device="cuda")
+    loss, g = net.loss_grad(xt, tt)
+    xn = ref.bf16(ref.normalise(x.astype(np.float32).astype(np.float64), LO.astype(np.float32), HI.astype(np.float32)))
+    loss_ref, g_ref = ref.loss_and_grad(_bf16_theta(w), xn, t.astype(np.float32).astype(np.float64))
+    assert loss == pytest.approx(loss_ref, rel=2e-2)
+    parts, parts_ref = ref.unpack(g.astype(np.float64)), ref.unpack(g_ref)
+    for name, a, b in zip(["W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"], parts, parts_ref):
+        err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert err < 5e-2, (name, err)
+    net.close()
+
+
+def test_training_fits_a_smooth_target(wlb):
+    import torch
+    x = _inputs(8192, 4)
+    t = np.sin(2 * x[:, 1]) * (1 - 1 / x[:, 3] ** 2) + 0.3 * x[:, 0]
+    net = wlb.MLP(LO, HI, batch_max=512)
+    net.init_weights(1)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    tt = torch.tensor(t, dtype=torch.float32, device="cuda")
+    hist = net.train(xt, tt, epochs=40, batch=512, lr=2e-3, lr_final=1e-4, seed=9)
+    assert hist[-1] < 0.05 * hist[0]
+    y, _ = net.predict(xt)
+    rms = float(np.sqrt(np.mean((y.cpu().numpy() - t) ** 2)))
+    assert rms < 0.05 * float(np.std(t)) + 0.02
+    net.close()
