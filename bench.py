@@ -381,6 +381,63 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def run_surrogate(args):
+    """Learned surrogate: 20k training and 2k held-out forces from the batched
+    2D lattice runs (512-lattice chunks of 192^2 D2Q5, 25 periods), training on
+    the tensor-core network, validation error, and 1M seeded queries."""
+    import numpy as np
+    import torch
+
+    from paper_2404_02346_gb300 import build as B
+    from paper_2404_02346_gb300 import surrogate as S
+
+    B.build()
+    train = workloads.surrogate_problems(20000, seed=args.seed)
+    val = workloads.surrogate_problems(2000, seed=args.seed + 1000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_train = S.lattice_targets(train)
+    t_val = S.lattice_targets(val)
+    torch.cuda.synchronize()
+    lb_s = time.perf_counter() - t0
+    sur = S.Surrogate(workloads.SURROGATE_BOX, batch_max=1 << 17)
+    t0 = time.perf_counter()
+    hist = sur.fit([p["features"] for p in train], t_train, epochs=args.epochs, batch=512)
+    train_s = time.perf_counter() - t0
+    y, _ = sur.predict([p["features"] for p in val])
+    err = y.cpu().numpy() - t_val
+    scale = float(np.abs(t_val).max())
+    q = torch.tensor(np.array(workloads.surrogate_queries(1 << 20, seed=args.seed + 2000), dtype=np.float32),
+                     device="cuda")
+    for _ in range(args.warmup):
+        sur.predict(q)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sur.predict(q)
+    torch.cuda.synchronize()
+    q_s = (time.perf_counter() - t0) / args.steps
+    sur.close()
+    lb_rate = (len(train) + len(val)) / lb_s
+    line = {
+        "metric": "radiation forces/s, learned surrogate", "value": (1 << 20) / q_s, "unit": "forces/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": q_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 weights/activations, fp32 accumulate (tcgen05)", "data": "synthetic",
+        "config": {"workload": "MLP 4-256-256-256-1 GELU; 20k train / 2k held-out 2D lattice forces "
+                               "(192^2 D2Q5, 25 periods); 1M seeded queries",
+                   "epochs": args.epochs, "batch": 512},
+        "lattice_forces_per_s_batched": lb_rate,
+        "speedup_vs_batched_lattice": (1 << 20) / q_s / lb_rate,
+        "train_s": train_s, "final_train_loss": float(hist[-1]),
+        "val_error": {"rms": float(np.sqrt(np.mean(err ** 2))), "max_abs": float(np.abs(err).max()),
+                      "target_scale_max_abs": scale,
+                      "rms_over_scale": float(np.sqrt(np.mean(err ** 2))) / scale,
+                      "frac_within_1pct_of_scale": float(np.mean(np.abs(err) <= 0.01 * scale))},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_profile(args, prob):
     """A short pass over the benchmark lattice for ncu: setup, 64 unsampled and
     64 sampled steps (graph-replayed where whole periods allow), the force."""
@@ -412,12 +469,16 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=64)
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"],
                     help="population storage (the benchmark workload is FP32)")
-    ap.add_argument("--workload", default="sphere256", choices=["sphere256", "ensemble3d", "ensemble2d"],
-                    help="sphere256: the benchmark line; ensembles: batched forces/s")
+    ap.add_argument("--workload", default="sphere256",
+                    choices=["sphere256", "ensemble3d", "ensemble2d", "surrogate"],
+                    help="sphere256: the benchmark line; ensembles: batched forces/s; surrogate: learned model")
+    ap.add_argument("--epochs", type=int, default=1500, help="surrogate training epochs")
     args = ap.parse_args()
     prob = workloads.sphere_3d(seed=args.seed, precision=args.precision)
     if args.profile:
         run_profile(args, prob)
+    elif args.workload == "surrogate":
+        run_surrogate(args)
     elif args.workload != "sphere256":
         run_ensemble(args)
     elif args.impl == "reference":

@@ -1,0 +1,71 @@
+"""The learned surrogate end to end at reduced size: lattice targets from the
+batched kernels, training on the tensor-core network, held-out error, the
+lattice fallback outside the training box, and the speed it gains."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+SMALL = dict(edge=96, n_surface=200, n_periods=8, n_avg_periods=3)
+
+
+@pytest.fixture(scope="module")
+def wlb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2404_02346_gb300 import build as B
+    B.build()
+    import paper_2404_02346_gb300 as W
+    W.lib()
+    return W
+
+
+def test_surrogate_pipeline(wlb):
+    import torch
+    from paper_2404_02346_gb300 import surrogate as S
+
+    train = workloads.surrogate_problems(1024, seed=1, **SMALL)
+    val = workloads.surrogate_problems(256, seed=2, **SMALL)
+    t0 = time.perf_counter()
+    t_train = S.lattice_targets(train)
+    t_val = S.lattice_targets(val)
+    lb_s = time.perf_counter() - t0
+    lb_rate = (len(train) + len(val)) / lb_s
+    # the closed form's shape: the normalised force follows (1 - kappa~) sin(2 k z0) in sign
+    kz = np.array([p["kz"] for p in train])
+    kap = np.array([p["kappa"] for p in train])
+    wei = (1 - kap) * np.sin(2 * kz)
+    strong = np.abs(wei) > 0.2
+    assert np.mean(np.sign(t_train[strong]) == np.sign(wei[strong])) > 0.9
+
+    sur = S.Surrogate(workloads.SURROGATE_BOX, batch_max=4096)
+    hist = sur.fit([p["features"] for p in train], t_train, epochs=400, batch=256, lr=2e-3, lr_final=2e-5)
+    assert hist[-1] < 0.05 * hist[0]
+    y, inside = sur.predict([p["features"] for p in val])
+    y = y.cpu().numpy()
+    assert inside.cpu().numpy().all()
+    rms = float(np.sqrt(np.mean((y - t_val) ** 2)))
+    assert rms < 0.1 * float(np.std(t_val)), (rms, np.std(t_val))
+
+    # outside the box: answered by the lattice method, identical to it
+    out_probs = [workloads.surrogate_problem(1.35, 0.7, 1.5, **SMALL),
+                 workloads.surrogate_problem(0.5, 1.1, 1.3, **SMALL)]
+    vals, used = sur.normalised_forces(out_probs)
+    assert list(used) == [True, False]
+    assert vals[0] == S.lattice_targets(out_probs[:1])[0]
+
+    # what the network gains: queries per second against lattice forces per second
+    q = torch.tensor(np.array(workloads.surrogate_queries(65536, seed=3), dtype=np.float32), device="cuda")
+    sur.predict(q)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        sur.predict(q)
+    torch.cuda.synchronize()
+    q_rate = 5 * 65536 / (time.perf_counter() - t0)
+    assert q_rate > 100 * lb_rate, (q_rate, lb_rate)
+    sur.close()

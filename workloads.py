@@ -151,3 +151,57 @@ def ensemble_2d(seed=1, count=512, edge=192, n_surface=1000, n_periods=25, n_avg
     g = SplitMix64(seed)
     return [_ensemble_member(g, 2, edge, n_surface, n_periods, n_avg_periods, precision)
             for _ in range(count)]
+
+
+# Learned-surrogate inputs: k R_p, k z0, sound-speed ratio (kappa~ = 1/c~^2).
+SURROGATE_BOX = {"ka": (0.1, 1.2), "kz": (0.0, math.pi), "c_ratio": (0.8, 2.0)}
+
+
+def latin_hypercube(n, dims, seed):
+    """n points in [0, 1)^dims, one per stratum on every axis (SplitMix64)."""
+    g = SplitMix64(seed)
+    cols = []
+    for _ in range(dims):
+        perm = list(range(n))
+        for i in range(n - 1, 0, -1):
+            j = int(g.uniform() * (i + 1))
+            perm[i], perm[j] = perm[j], perm[i]
+        cols.append([(perm[i] + g.uniform()) / n for i in range(n)])
+    return [[cols[d][i] for d in range(dims)] for i in range(n)]
+
+
+def surrogate_problem(ka, kz, c_ratio, edge=192, n_surface=1000, n_periods=25, n_avg_periods=10,
+                      precision="f32"):
+    """2D cylinder on an edge^2 lattice (lambda = edge/2) for the given features."""
+    lam = edge / 2.0
+    k = 2.0 * math.pi / lam
+    R = quantise(ka / k)
+    z0 = kz / k
+    p = problem(2, (edge, edge), 1, lam, R, (edge / 2.0, z0), cp=c_ratio * 0.25, n_surface=n_surface,
+                n_periods=n_periods, n_avg_periods=n_avg_periods, precision=precision)
+    p.update({"ka": k * R, "kz": kz, "c_ratio": c_ratio, "kappa": 1.0 / c_ratio ** 2,
+              "features": (k * R, kz, 1.0 / c_ratio ** 2, c_ratio)})
+    return p
+
+
+def surrogate_problems(n, seed, **kw):
+    """Seeded Latin-hypercube sample of the surrogate's input box."""
+    (a0, a1), (z0, z1), (c0, c1) = (SURROGATE_BOX[k] for k in ("ka", "kz", "c_ratio"))
+    return [surrogate_problem(a0 + (a1 - a0) * u[0], z0 + (z1 - z0) * u[1], c0 + (c1 - c0) * u[2], **kw)
+            for u in latin_hypercube(n, 3, seed)]
+
+
+def surrogate_queries(n, seed, outside_fraction=0.0):
+    """n feature rows (k R, k z0, kappa~, c~) drawn uniformly in the box; a
+    fraction of them pushed outside (k R beyond the trained range)."""
+    g = SplitMix64(seed)
+    (a0, a1), (z0, z1), (c0, c1) = (SURROGATE_BOX[k] for k in ("ka", "kz", "c_ratio"))
+    rows = []
+    for i in range(n):
+        ka = a0 + (a1 - a0) * g.uniform()
+        kz = z0 + (z1 - z0) * g.uniform()
+        c = c0 + (c1 - c0) * g.uniform()
+        if g.uniform() < outside_fraction:
+            ka = a1 + 0.1 + 0.2 * g.uniform()
+        rows.append((ka, kz, 1.0 / c ** 2, c))
+    return rows
