@@ -281,7 +281,10 @@ def run_gpu(args, prob):
     else:
         peak, peak_src = 6800.0, "fallback"
     traffic = _traffic(_kernel_sha()) if args.precision == "f32" else None
-    launches = args.steps * (2 + n_free + 2 * n_window + n_avg + 1)
+    # per force: 3 setup kernels, one update launch per step (sampling fused into
+    # it on the row-vectorised path), one fold per averaged period, the force
+    per_step = 3 + n_steps + (0 if info.vector_path else n_window) + n_avg + 1
+    launches = args.steps * per_step
     if rank == 0:
         line = {
             "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world,
@@ -438,6 +441,63 @@ def run_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """512^3 D3Q7 force-vs-position sweep: 16 positions k z0 = j pi / 15, run one
+    after another, for each requested storage precision; F(kz) against the
+    sin(2 k z0) law and the FP16 - FP32 difference per position."""
+    import math
+
+    import torch
+
+    import paper_2404_02346_gb300 as wlb
+    from paper_2404_02346_gb300 import build as B
+
+    B.build()
+    stream = torch.cuda.Stream()
+    precs = ["f32", "f16"] if args.precision == "f32" else [args.precision]
+    res = {}
+    lu = 0
+    t_all = {}
+    for prec in precs:
+        forces = []
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        cells = 512 ** 3
+        start.record(stream)
+        for j in range(16):
+            prob = workloads.sphere_3d_large(position=j, precision=prec)
+            with wlb.Solver(prob, stream=stream) as sj:
+                forces.append(float(sj.run()[2]))
+                steps = sj.info().n_steps
+        end.record(stream)
+        torch.cuda.synchronize()
+        t_all[prec] = start.elapsed_time(end) * 1e-3
+        res[prec] = forces
+        lu = cells * steps * 16
+    f32 = res.get("f32")
+    fit = None
+    if f32:
+        amp = max(abs(v) for v in f32)
+        kz = [j * math.pi / 15 for j in range(16)]
+        # least-squares amplitude of the sin(2 k z0) law and the residual
+        a = sum(f * math.sin(2 * k) for f, k in zip(f32, kz)) / sum(math.sin(2 * k) ** 2 for k in kz)
+        resid = max(abs(f - a * math.sin(2 * k)) for f, k in zip(f32, kz)) / amp
+        fit = {"amplitude": a, "max_residual_over_amplitude": resid}
+    line = {
+        "metric": "512^3 force-vs-position sweep", "value": lu / t_all[precs[0]] / 1e9, "unit": "GLUPS",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": t_all[precs[0]] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precs[0], "data": "synthetic",
+        "config": {"workload": "512^3 D3Q7, lambda=256, R=24, 4096 points, kappa~=0.5, 16 positions x 30 periods"},
+        "forces": res, "sin2kz_fit_f32": fit,
+        "seconds": t_all,
+        "glups": {p: lu / t_all[p] / 1e9 for p in precs},
+    }
+    if "f16" in res and f32:
+        amp = max(abs(v) for v in f32)
+        line["f16_minus_f32_over_amplitude"] = [abs(a - b) / amp for a, b in zip(res["f16"], f32)]
+    print(json.dumps(line), flush=True)
+
+
 def run_profile(args, prob):
     """A short pass over the benchmark lattice for ncu: setup, 64 unsampled and
     64 sampled steps (graph-replayed where whole periods allow), the force."""
@@ -470,7 +530,7 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"],
                     help="population storage (the benchmark workload is FP32)")
     ap.add_argument("--workload", default="sphere256",
-                    choices=["sphere256", "ensemble3d", "ensemble2d", "surrogate"],
+                    choices=["sphere256", "ensemble3d", "ensemble2d", "surrogate", "sweep512"],
                     help="sphere256: the benchmark line; ensembles: batched forces/s; surrogate: learned model")
     ap.add_argument("--epochs", type=int, default=1500, help="surrogate training epochs")
     args = ap.parse_args()
@@ -479,6 +539,8 @@ def main():
         run_profile(args, prob)
     elif args.workload == "surrogate":
         run_surrogate(args)
+    elif args.workload == "sweep512":
+        run_sweep(args)
     elif args.workload != "sphere256":
         run_ensemble(args)
     elif args.impl == "reference":

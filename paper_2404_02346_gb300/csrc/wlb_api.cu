@@ -107,6 +107,7 @@ size_t layout(const Geometry &g, Prec prec, char *base, Buffers *b) {
     t.acc64 = (double *)take(N * 5 * sizeof(double));
     t.force = (double *)take(4 * sizeof(double));
     t.err = (int *)take(sizeof(int));
+    t.ptab = (double *)take(sizeof(double) * g.n[g.wave_axis]);
     t.stage_cells = g.ncell < kStageCells ? g.ncell : kStageCells;
     t.stage = (double *)take((size_t)t.stage_cells * (1 + g.dim) * sizeof(double));
     if (b) *b = t;
@@ -133,12 +134,7 @@ void destroy_graphs(wlb_handle *h) {
 cudaError_t issue_period(wlb_handle *h, int start, bool sampled, cudaStream_t s) {
     int cur = start;
     for (long long t = 0; t < h->period; ++t) {
-        cudaError_t e;
-        if (sampled) {
-            e = wlb::launch_sample(h->g, h->b, h->prec, cur, s);
-            if (e != cudaSuccess) return e;
-        }
-        e = wlb::launch_update(h->g, h->b, h->prec, cur, s, nullptr);
+        cudaError_t e = wlb::launch_step(h->g, h->b, h->prec, cur, sampled, s);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
@@ -298,8 +294,7 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
             n -= h->period;
             continue;
         }
-        if (sampled) WLB_CUDA(h, wlb::launch_sample(h->g, h->b, h->prec, h->src, h->stream), "sample kernel");
-        WLB_CUDA(h, wlb::launch_update(h->g, h->b, h->prec, h->src, h->stream, nullptr), "update kernel");
+        WLB_CUDA(h, wlb::launch_step(h->g, h->b, h->prec, h->src, sampled, h->stream), "step kernels");
         h->src ^= 1;
         h->steps_done += 1;
         if (sampled) {

@@ -46,6 +46,7 @@ struct Buffers {
     double *acc64;         // n_surface * 5: folded sums
     double *force;         // 4 doubles
     int *err;              // 1 int: non-finite accumulator seen
+    double *ptab;          // n[wave_axis]: incident pressure along the wave axis (setup)
     double *stage;         // stage_cells * (1 + dim): field read-back staging
     long long stage_cells;
 };
@@ -55,6 +56,9 @@ cudaError_t launch_setup(const Geometry &g, const Buffers &b, Prec p, cudaStream
 cudaError_t launch_update(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s,
                           bool *vector_path);
 cudaError_t launch_sample(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s);
+// One whole step: the update, plus the surface sampling of the same input when
+// sample is set (fused into the update launch on the row-vectorised path).
+cudaError_t launch_step(const Geometry &g, const Buffers &b, Prec p, int src, bool sample, cudaStream_t s);
 cudaError_t launch_fold(const Geometry &g, const Buffers &b, Prec p, cudaStream_t s);
 cudaError_t launch_force(const Geometry &g, const Buffers &b, double n_window, cudaStream_t s);
 cudaError_t launch_fields(const Geometry &g, const Buffers &b, Prec p, int src,

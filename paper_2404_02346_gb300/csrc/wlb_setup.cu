@@ -53,11 +53,12 @@ __device__ double sound_speed_sq(const Geometry &g, int x, int y, int z) {
     return c * c;
 }
 
-// Standing-wave pressure at t = 0 (Eq. 38, s measured from an antinode).
-__device__ double incident_pressure(const Geometry &g, int x, int y, int z) {
-    const int c[3] = {x, y, z};
-    double s = (double)c[g.wave_axis] - g.antinode;
-    return g.p_a * cos(2.0 * kPi * s / g.wavelength);
+// Standing-wave pressure at t = 0 (Eq. 38, s measured from an antinode), one
+// value per coordinate along the wave axis.
+__global__ void incident_table(Geometry g, double *__restrict__ ptab) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n[g.wave_axis]) return;
+    ptab[s] = g.p_a * cos(2.0 * kPi * ((double)s - g.antinode) / g.wavelength);
 }
 
 // Conversion of an FP64 value to the storage type (round to nearest).
@@ -70,7 +71,7 @@ template <> __device__ __forceinline__ __half to_store<__half>(double v) { retur
 // times the storage scale.
 template <typename S, typename T>
 __global__ void setup_cells(Geometry g, S *__restrict__ pop, uint8_t *__restrict__ cls,
-                            T *__restrict__ c2f) {
+                            T *__restrict__ c2f, const double *__restrict__ ptab) {
     long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= g.ncell) return;
     int x = (int)(id % g.n[0]);
@@ -81,14 +82,16 @@ __global__ void setup_cells(Geometry g, S *__restrict__ pop, uint8_t *__restrict
     cls[id] = cell_class(g, q);
     double c2 = sound_speed_sq(g, x, y, z);
     c2f[id] = (T)c2;
-    double p = incident_pressure(g, x, y, z);
+    const int cc[3] = {x, y, z};
+    const int ax = g.wave_axis;
+    double p = ptab[cc[ax]];
     pop[id] = to_store<S>((p / c2) * (1.0 - g.dim * c2) * g.pop_scale);  // f_0^eq = rho1 (1 - D c^2)
     for (int i = 1; i < g.q; ++i) {
         int a = (i - 1) >> 1;
         int v = ((i - 1) & 1) ? -1 : 1;
         int c[3] = {x, y, z};
         c[a] = wrap_index(c[a] + v, g.n[a]);
-        double pn = incident_pressure(g, c[0], c[1], c[2]);
+        double pn = ptab[c[ax]];
         pop[(long long)i * g.ncell + id] = to_store<S>(0.5 * pn * g.pop_scale);  // f_i^eq = c^2 rho1 / 2
     }
 }
@@ -194,7 +197,11 @@ template <typename S, typename T>
 cudaError_t setup_impl(const Geometry &g, const Buffers &b, cudaStream_t s) {
     const int tb = 256;
     long long blocks = (g.ncell + tb - 1) / tb;
-    setup_cells<S, T><<<(unsigned)blocks, tb, 0, s>>>(g, (S *)b.pop[0], b.cls, (T *)b.c2);
+    const int ns = g.n[g.wave_axis];
+    incident_table<<<(ns + 127) / 128, 128, 0, s>>>(g, b.ptab);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
+    setup_cells<S, T><<<(unsigned)blocks, tb, 0, s>>>(g, (S *)b.pop[0], b.cls, (T *)b.c2, b.ptab);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (g.n_surface > 0) {

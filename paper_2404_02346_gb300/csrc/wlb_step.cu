@@ -21,21 +21,89 @@
 namespace wlb {
 namespace {
 
+// One warp per surface element; lane l < 3^dim handles stencil cell l.
+// P = sum_l delta_l c_l^2 rho1_l and U = sum_l delta_l J1_l / rho0 (Eqs. 80-81),
+// then acc += (P^2, U.U, U_x (U.n), U_y (U.n), U_z (U.n)) in stored units.
+template <typename S>
+struct SampleArgs {
+    Geometry g;
+    const int4 *st_xyz;
+    const typename Store<S>::R *st_w, *nrm;
+    typename Store<S>::R *acc;
+};
+
+template <typename S>
+__device__ __forceinline__ void sample_point(const SampleArgs<S> &a, const S *__restrict__ src, int k, int lane) {
+    using R = typename Store<S>::R;
+    const Geometry &g = a.g;
+    R p = R(0), u[3] = {R(0), R(0), R(0)};
+    if (lane < g.stencil) {
+        const long long o = (long long)k * g.stencil + lane;
+        const int4 c = a.st_xyz[o];
+        R rho, J[3];
+        pulled_moments(g, src, c.x, c.y, c.z, rho, J);
+        const R wp = a.st_w[2 * o], wu = a.st_w[2 * o + 1];
+        p = wp * rho;
+        u[0] = wu * J[0];
+        u[1] = wu * J[1];
+        u[2] = wu * J[2];
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        p += __shfl_xor_sync(kFull, p, m);
+        u[0] += __shfl_xor_sync(kFull, u[0], m);
+        u[1] += __shfl_xor_sync(kFull, u[1], m);
+        u[2] += __shfl_xor_sync(kFull, u[2], m);
+    }
+    if (lane == 0) {
+        const R nx = a.nrm[4 * k], ny = a.nrm[4 * k + 1], nz = a.nrm[4 * k + 2];
+        const R un = u[0] * nx + u[1] * ny + u[2] * nz;
+        R *acc = a.acc + 5 * (long long)k;
+        acc[0] += p * p;
+        acc[1] += u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        acc[2] += u[0] * un;
+        acc[3] += u[1] * un;
+        acc[4] += u[2] * un;
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) sample_points(SampleArgs<S> a, const S *__restrict__ src) {
+    const int lane = threadIdx.x & 31;
+    const int k = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (k >= a.g.n_surface) return;  // uniform per warp
+    sample_point(a, src, k, lane);
+}
+
 // Row-vectorised update.  One warp owns one lattice row (fixed y, z) of
 // nx = 32 * W * CH cells; lane L holds cells (c*32 + L)*W .. +W-1 of chunk c.
 // Every population row is read with aligned 16-byte loads: the +-y and +-z
 // neighbours are whole rows, and the +-x shift (including the periodic wrap at
 // the row ends) is done with warp shuffles, so no element is loaded twice.
+//
+// Blocks at or beyond row_blocks sample the surface instead (one warp per
+// point): they read the same input buffer and write only the running sums, so
+// the sampled step is one launch.  Launched with programmatic dependent
+// launch: every block lets the next launch start, then waits for the previous
+// one to finish before reading.
 template <typename S, int D, int CH>
 __global__ void __launch_bounds__(256) update_rows(const S *__restrict__ src, S *__restrict__ dst,
                                                    const uint8_t *__restrict__ cls,
                                                    const typename Store<S>::R *__restrict__ c2f, int nx,
                                                    int ny, int nz, long long ncell,
-                                                   typename Store<S>::R c0sq, typename Store<S>::R cpsq) {
+                                                   typename Store<S>::R c0sq, typename Store<S>::R cpsq,
+                                                   long long row_blocks, SampleArgs<S> sa) {
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
     constexpr int Q = 2 * D + 1;
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31;
+    if ((long long)blockIdx.x >= row_blocks) {
+        const int k = (int)((((long long)blockIdx.x - row_blocks) * blockDim.x + threadIdx.x) >> 5);
+        if (k < sa.g.n_surface) sample_point(sa, src, k, lane);
+        return;
+    }
     const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= (long long)ny * nz) return;  // uniform per warp
     const int y = (int)(row % ny);
@@ -156,50 +224,6 @@ __global__ void __launch_bounds__(256) update_cells(const S *__restrict__ src, S
     }
 }
 
-// One warp per surface element; lane l < 3^dim handles stencil cell l.
-// P = sum_l delta_l c_l^2 rho1_l and U = sum_l delta_l J1_l / rho0 (Eqs. 80-81),
-// then acc += (P^2, U.U, U_x (U.n), U_y (U.n), U_z (U.n)) in stored units.
-template <typename S>
-__global__ void __launch_bounds__(256) sample_points(Geometry g, const S *__restrict__ src,
-                                                     const int4 *__restrict__ st_xyz,
-                                                     const typename Store<S>::R *__restrict__ st_w,
-                                                     const typename Store<S>::R *__restrict__ nrm,
-                                                     typename Store<S>::R *__restrict__ acc) {
-    using R = typename Store<S>::R;
-    const int lane = threadIdx.x & 31;
-    const int k = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (k >= g.n_surface) return;  // uniform per warp
-    R p = R(0), u[3] = {R(0), R(0), R(0)};
-    if (lane < g.stencil) {
-        const long long o = (long long)k * g.stencil + lane;
-        const int4 c = st_xyz[o];
-        R rho, J[3];
-        pulled_moments(g, src, c.x, c.y, c.z, rho, J);
-        const R wp = st_w[2 * o], wu = st_w[2 * o + 1];
-        p = wp * rho;
-        u[0] = wu * J[0];
-        u[1] = wu * J[1];
-        u[2] = wu * J[2];
-    }
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        p += __shfl_xor_sync(kFull, p, m);
-        u[0] += __shfl_xor_sync(kFull, u[0], m);
-        u[1] += __shfl_xor_sync(kFull, u[1], m);
-        u[2] += __shfl_xor_sync(kFull, u[2], m);
-    }
-    if (lane == 0) {
-        const R nx = nrm[4 * k], ny = nrm[4 * k + 1], nz = nrm[4 * k + 2];
-        const R un = u[0] * nx + u[1] * ny + u[2] * nz;
-        R *a = acc + 5 * (long long)k;
-        a[0] += p * p;
-        a[1] += u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        a[2] += u[0] * un;
-        a[3] += u[1] * un;
-        a[4] += u[2] * un;
-    }
-}
-
 // acc64 += acc * scale (scale = 1 / pop_scale^2 converts stored units back).
 template <typename R>
 __global__ void fold_sums(int n, R *__restrict__ acc, double *__restrict__ acc64, double scale,
@@ -266,15 +290,38 @@ __global__ void read_fields(Geometry g, const S *__restrict__ src, const uint8_t
     for (int a = 0; a < g.dim; ++a) stage[(long long)(1 + a) * count + j] = (double)J[a] * unscale / g.rho0;
 }
 
+template <typename S>
+SampleArgs<S> sample_args(const Geometry &g, const Buffers &b) {
+    using R = typename Store<S>::R;
+    SampleArgs<S> a;
+    a.g = g;
+    a.st_xyz = b.st_xyz;
+    a.st_w = (const R *)b.st_w;
+    a.nrm = (const R *)b.nrm;
+    a.acc = (R *)b.acc;
+    return a;
+}
+
+// Update launch (rows, plus sampling blocks when sample is set) with the
+// programmatic-serialization attribute.
 template <typename S, int D, int CH>
-cudaError_t run_rows(const Geometry &g, const Buffers &b, int src, cudaStream_t s) {
+cudaError_t run_rows(const Geometry &g, const Buffers &b, int src, bool sample, cudaStream_t s) {
     using R = typename Store<S>::R;
     const long long rows = (long long)g.n[1] * g.n[2];
-    const long long blocks = (rows * 32 + 255) / 256;
-    update_rows<S, D, CH><<<(unsigned)blocks, 256, 0, s>>>(
-        (const S *)b.pop[src], (S *)b.pop[src ^ 1], b.cls, (const R *)b.c2, g.n[0], g.n[1], g.n[2],
-        g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp));
-    return cudaGetLastError();
+    const long long row_blocks = (rows * 32 + 255) / 256;
+    const long long sample_blocks = sample && g.n_surface > 0 ? (g.n_surface + 7) / 8 : 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(row_blocks + sample_blocks));
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, update_rows<S, D, CH>, (const S *)b.pop[src], (S *)b.pop[src ^ 1],
+                              (const uint8_t *)b.cls, (const R *)b.c2, g.n[0], g.n[1], g.n[2], g.ncell,
+                              (R)(g.c0 * g.c0), (R)(g.cp * g.cp), row_blocks, sample_args<S>(g, b));
 }
 
 template <typename S>
@@ -286,15 +333,15 @@ int row_chunks(const Geometry &g) {
 }
 
 template <typename S, int D>
-cudaError_t run_update(const Geometry &g, const Buffers &b, int src, cudaStream_t s, bool *vec) {
+cudaError_t run_update(const Geometry &g, const Buffers &b, int src, bool sample, cudaStream_t s, bool *vec) {
     using R = typename Store<S>::R;
     const int ch = row_chunks<S>(g);
     *vec = ch > 0;
     switch (ch) {
-        case 1: return run_rows<S, D, 1>(g, b, src, s);
-        case 2: return run_rows<S, D, 2>(g, b, src, s);
-        case 3: return run_rows<S, D, 3>(g, b, src, s);
-        case 4: return run_rows<S, D, 4>(g, b, src, s);
+        case 1: return run_rows<S, D, 1>(g, b, src, sample, s);
+        case 2: return run_rows<S, D, 2>(g, b, src, sample, s);
+        case 3: return run_rows<S, D, 3>(g, b, src, sample, s);
+        case 4: return run_rows<S, D, 4>(g, b, src, sample, s);
         default: break;
     }
     const long long blocks = (g.ncell + 255) / 256;
@@ -305,16 +352,14 @@ cudaError_t run_update(const Geometry &g, const Buffers &b, int src, cudaStream_
 }
 
 template <typename S>
-cudaError_t update_for(const Geometry &g, const Buffers &b, int src, cudaStream_t s, bool *vec) {
-    return g.dim == 3 ? run_update<S, 3>(g, b, src, s, vec) : run_update<S, 2>(g, b, src, s, vec);
+cudaError_t update_for(const Geometry &g, const Buffers &b, int src, bool sample, cudaStream_t s, bool *vec) {
+    return g.dim == 3 ? run_update<S, 3>(g, b, src, sample, s, vec) : run_update<S, 2>(g, b, src, sample, s, vec);
 }
 
 template <typename S>
 cudaError_t sample_for(const Geometry &g, const Buffers &b, int src, cudaStream_t s) {
-    using R = typename Store<S>::R;
     const unsigned blocks = (unsigned)((g.n_surface + 7) / 8);
-    sample_points<S><<<blocks, 256, 0, s>>>(g, (const S *)b.pop[src], b.st_xyz, (const R *)b.st_w,
-                                            (const R *)b.nrm, (R *)b.acc);
+    sample_points<S><<<blocks, 256, 0, s>>>(sample_args<S>(g, b), (const S *)b.pop[src]);
     return cudaGetLastError();
 }
 
@@ -343,12 +388,25 @@ cudaError_t launch_update(const Geometry &g, const Buffers &b, Prec p, int src, 
     bool vec = false;
     cudaError_t e;
     switch (p) {
-        case Prec::F64: e = update_for<double>(g, b, src, s, &vec); break;
-        case Prec::F16: e = update_for<__half>(g, b, src, s, &vec); break;
-        default: e = update_for<float>(g, b, src, s, &vec); break;
+        case Prec::F64: e = update_for<double>(g, b, src, false, s, &vec); break;
+        case Prec::F16: e = update_for<__half>(g, b, src, false, s, &vec); break;
+        default: e = update_for<float>(g, b, src, false, s, &vec); break;
     }
     if (vector_path) *vector_path = vec;
     return e;
+}
+
+cudaError_t launch_step(const Geometry &g, const Buffers &b, Prec p, int src, bool sample, cudaStream_t s) {
+    if (!sample || g.n_surface == 0 || !update_is_vectorised(g, p)) {
+        cudaError_t e = sample && g.n_surface > 0 ? launch_sample(g, b, p, src, s) : cudaSuccess;
+        return e == cudaSuccess ? launch_update(g, b, p, src, s, nullptr) : e;
+    }
+    bool vec = false;
+    switch (p) {
+        case Prec::F64: return update_for<double>(g, b, src, true, s, &vec);
+        case Prec::F16: return update_for<__half>(g, b, src, true, s, &vec);
+        default: return update_for<float>(g, b, src, true, s, &vec);
+    }
 }
 
 cudaError_t launch_sample(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s) {
