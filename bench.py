@@ -52,10 +52,11 @@ def _peaks():
         return None
 
 
-def _traffic(kernel_src_sha):
+def _traffic(kernel_src_sha, steps_per_launch=1):
     """Per-launch DRAM bytes of the update kernel from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "update_rows_d3q7_f32_256cubed.md")
+    name = "update2_slab_d3q7_f32_256cubed.md" if steps_per_launch == 2 else "update_rows_d3q7_f32_256cubed.md"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         text = open(path).read()
     except OSError:
@@ -73,8 +74,9 @@ def _traffic(kernel_src_sha):
         return None
 
 
-def _kernel_sha():
-    src = os.path.join(ROOT, "paper_2404_02346_gb300", "csrc", "wlb_step.cu")
+def _kernel_sha(steps_per_launch=1):
+    name = "wlb_two_step.cu" if steps_per_launch == 2 else "wlb_step.cu"
+    src = os.path.join(ROOT, "paper_2404_02346_gb300", "csrc", name)
     return hashlib.sha256(open(src, "rb").read()).hexdigest()
 
 
@@ -219,6 +221,10 @@ def run_gpu(args, prob):
     stream = torch.cuda.Stream()
     cells = prob["n"][0] * prob["n"][1] * prob["n"][2]
     solver = wlb.Solver(prob, stream=stream)
+    if args.single_step:
+        solver.set_two_step(False)
+    elif args.slab_rows:
+        solver.set_two_step(True, args.slab_rows)
     info = solver.info()
     n_steps, n_window = info.n_steps, info.n_window
     n_free = n_steps - n_window
@@ -256,7 +262,10 @@ def run_gpu(args, prob):
     barrier()
     clk = clocks.stop()
     ms = start.elapsed_time(end)
-    k1_ms = sum(a.elapsed_time(b) for a, b in k1) / (args.steps * n_free)
+    # average duration of one update launch in the unsampled phase (one or two
+    # steps per launch)
+    spl = info.steps_per_launch
+    k1_ms = sum(a.elapsed_time(b) for a, b in k1) / (args.steps * n_free) * spl
     ms, lu = job_totals(ms, cells * n_steps * args.steps, world, device="cuda")
     glups = lu / (ms * 1e-3) / 1e9
     forces_per_s = lu / (cells * n_steps) / (ms * 1e-3)
@@ -274,16 +283,19 @@ def run_gpu(args, prob):
            "forces_per_s": e2e_steps / e2e_s, "force": [float(v) for v in Fe]}
 
     peaks = _peaks()
+    # algorithmic HBM bytes of one update launch: every population read and
+    # written once (a double-step launch keeps the intermediate state in L2),
+    # plus the class byte
     bpu = info.bytes_per_update
     achieved = bpu * cells / (k1_ms * 1e-3) / 1e9
     if peaks and "hbm_gbs" in peaks:
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    traffic = _traffic(_kernel_sha()) if args.precision == "f32" else None
+    traffic = _traffic(_kernel_sha(spl), spl) if args.precision == "f32" else None
     # per force: 3 setup kernels, one update launch per step (sampling fused into
     # it on the row-vectorised path), one fold per averaged period, the force
-    per_step = 3 + n_steps + (0 if info.vector_path else n_window) + n_avg + 1
+    per_step = 3 + n_window + n_free // spl + (0 if info.vector_path else n_window) + n_avg + 1
     launches = args.steps * per_step
     if rank == 0:
         line = {
@@ -300,7 +312,9 @@ def run_gpu(args, prob):
             "force": [float(v) for v in F],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "update_rows (%s storage)" % args.precision, "bytes_per_cell": bpu,
+                         "kernel": ("update2_slab, 2 steps/launch, %d-row slabs" % info.two_step_rows
+                                    if spl == 2 else "update_rows")
+                                   + " (%s storage)" % args.precision, "bytes_per_cell_per_launch": bpu,
                          "avg_launch_us": k1_ms * 1e3, "peak_source": peak_src + " hbm_gbs"},
             "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
@@ -509,6 +523,10 @@ def run_profile(args, prob):
     B.build()
     stream = torch.cuda.Stream()
     with wlb.Solver(prob, stream=stream) as s:
+        if args.single_step:
+            s.set_two_step(False)
+        elif args.slab_rows:
+            s.set_two_step(True, args.slab_rows)
         s.init()
         s.step(args.profile_steps, sample=False)
         s.step(args.profile_steps, sample=True)
@@ -525,6 +543,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single-step", action="store_true",
+                    help="one step per update launch (default: unsampled steps two per launch)")
+    ap.add_argument("--slab-rows", type=int, default=0, help="slab height of the two-step kernel (0: automatic)")
     ap.add_argument("--profile", action="store_true", help="short pass for ncu captures")
     ap.add_argument("--profile-steps", type=int, default=64)
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"],

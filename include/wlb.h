@@ -54,6 +54,9 @@ typedef enum {
 } wlb_status;
 
 typedef enum { WLB_D2Q5 = 0, WLB_D3Q7 = 1 } wlb_lattice;          /* Fig. 8   */
+/* Geometry along the wave axis: fully periodic with the standing wave as the
+ * initial state, or the driven cavity of Sec. VII (see wlb_params). */
+typedef enum { WLB_BOUNDARY_PERIODIC = 0, WLB_BOUNDARY_DRIVEN = 1 } wlb_boundary;
 /* Storage and arithmetic of the populations: FP32, FP64, or FP16 storage of
  * f / p_a (the deviation from the rest state f = 0, scaled to O(1)) with FP32
  * arithmetic, running sums and sound-speed field. */
@@ -82,7 +85,20 @@ typedef enum { WLB_POP_F32 = 0, WLB_POP_F64 = 1, WLB_POP_F16 = 2 } wlb_precision
  *   n_surface      N surface elements: equal arcs in 2D, Fibonacci points in 3D.
  *   n_periods      total run length in periods T.
  *   n_avg_periods  the last n_avg_periods periods are averaged (<= n_periods).
- *   precision      WLB_POP_F32, WLB_POP_F64 or WLB_POP_F16 (p_a != 0).
+ *   precision      WLB_POP_F32, WLB_POP_F64 or WLB_POP_F16 (p_a != 0; p_a
+ *                  sets the FP16 storage scale).
+ *   boundary       WLB_BOUNDARY_PERIODIC, or WLB_BOUNDARY_DRIVEN: the driven
+ *                  cavity of Sec. VII along wave_axis, starting from rest:
+ *                  the planes s = 0 and s = n-1 are partially absorbing walls
+ *                  (bounce-back damped by wall_damping, Eq. 73; the value that
+ *                  would leave the domain is dropped), the plane s = 1 is a
+ *                  source sheet where the fields are imposed after collision
+ *                  (Eq. 72): rho1 = source_amplitude sin(2 pi (t mod T)/T),
+ *                  J1 from Eq. (62).  The box length along wave_axis is free
+ *                  (the paper uses lambda/2 + 3); the object, its band and
+ *                  stencil must lie in 2 <= s <= n-2; antinode is ignored.
+ *   wall_damping   Phi in [0, 1] (the paper uses 0.99).
+ *   source_amplitude  rho_a of the source sheet.
  *
  * The object, its interface band and the interpolation stencil must fit in
  * half the box along every axis (minimum-image distances must be unique).
@@ -98,6 +114,8 @@ typedef struct {
     int n_surface;
     int n_periods, n_avg_periods;
     int precision;
+    int boundary;
+    double wall_damping, source_amplitude;
 } wlb_params;
 
 typedef struct wlb_handle wlb_handle;
@@ -115,6 +133,9 @@ typedef struct {
                                    2 q pop_bytes + 1 (class byte); pop_bytes is
                                    4, 8 or 2                                   */
     int vector_path;            /* 1 if the row-vectorised update kernel is used */
+    int steps_per_launch;       /* unsampled steps per update launch: 1, or 2
+                                   with wlb_set_two_step                        */
+    int two_step_rows;          /* slab height of the two-step kernel, 0 off    */
 } wlb_info;
 
 /* Check a parameter set.  WLB_ERR_ARG for: unknown lattice or precision,
@@ -173,7 +194,8 @@ wlb_status wlb_fields(wlb_handle *h, double *p1_out, double *u1_out);
 wlb_status wlb_surface(wlb_handle *h, double *pts_out);
 
 /* Cell classes after wlb_init: nx*ny*nz bytes [z][y][x] (host buffer):
- * 0 fluid (c = c0), 1 object (c = cp), 2 interface band (c from Eq. 79).
+ * 0 fluid (c = c0), 1 object (c = cp), 2 interface band (c from Eq. 79);
+ * with WLB_BOUNDARY_DRIVEN also 3 low wall, 4 high wall, 5 source sheet.
  * A cell is fluid when (|x - r0|^2 - R_p^2) >= 20 d, object when it is
  * <= -20 d, band otherwise (minimum-image distance); beyond the band the tanh
  * of Eq. (79) is +-1 in double precision.  Synchronises. */
@@ -241,7 +263,8 @@ wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, double force_ou
  *                              WLB_ERR_UNSTABLE if any lattice's sums are not
  *                              finite.
  * WLB_ERR_ARG for count < 1, an invalid parameter set, mixed lattice types or
- * precisions, or a row length the batched update does not cover.
+ * precisions, a row length the batched update does not cover, or a driven
+ * geometry (batches are periodic only).
  */
 typedef struct wlb_batch wlb_batch;
 typedef struct {
@@ -313,6 +336,22 @@ wlb_status wlb_mlp_destroy(wlb_mlp *m);
 
 /* Sizes and counters of a handle. */
 wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
+
+/* Unsampled steps two per launch: the update of Eqs. (62)-(64), (71) applied
+ * twice in one kernel, bit-identical to two single steps.  Each block owns a
+ * slab of slab_rows rows (y) of a range of planes (z); it computes the first
+ * step on its rows plus one halo row on either side and keeps that state on
+ * the SM, so the populations cross HBM about once per two steps.  No block
+ * waits for another.  Sampled steps stay single.  On by default (set up by
+ * wlb_create with an automatic slab height) wherever it is supported.
+ * Supported: 3D, periodic boundaries, FP32 rows of nx = 128 or 256 cells or
+ * FP16 rows of nx = 256 (one warp per row); otherwise WLB_ERR_ARG.
+ * enable: 0 off, nonzero on.  slab_rows: 0 lets the library choose (largest
+ * slab the shared memory holds, chunking z to fill the SMs), else that height
+ * (WLB_ERR_ARG if it does not fit).  A stalled staging copy (bounded wait)
+ * makes wlb_force return WLB_ERR_TIMEOUT.  The paper has no counterpart: it
+ * is a memory-traffic optimisation of the same update. */
+wlb_status wlb_set_two_step(wlb_handle *h, int enable, int slab_rows);
 
 /* Release the handle, its graphs, streams and any memory it allocated. */
 wlb_status wlb_destroy(wlb_handle *h);

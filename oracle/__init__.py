@@ -36,6 +36,9 @@ class _Problem(ctypes.Structure):
         ("n_surface", ctypes.c_int),
         ("n_steps", ctypes.c_long),
         ("n_window", ctypes.c_long),
+        ("driven", ctypes.c_int),
+        ("wall_damping", ctypes.c_double),
+        ("source_amplitude", ctypes.c_double),
     ]
 
 
@@ -58,6 +61,7 @@ def lib():
         L.orc_macroscopic.argtypes = [pp, dp, dp, dp]
         L.orc_collide.argtypes = [pp, dp, dp, dp]
         L.orc_advect.argtypes = [pp, dp, dp]
+        L.orc_apply_boundaries.argtypes = [pp, dp, dp, dp, ctypes.c_long]
         L.orc_interpolate.argtypes = [pp, dp, dp, dp, dp, dp, dp]
         L.orc_force.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
@@ -86,6 +90,9 @@ def _struct(prob):
     s.n_surface = int(prob["n_surface"])
     s.n_steps = int(prob["n_steps"])
     s.n_window = int(prob["n_window"])
+    s.driven = 1 if prob.get("boundary", "periodic") == "driven" else 0
+    s.wall_damping = float(prob.get("wall_damping", 0.99))
+    s.source_amplitude = float(prob.get("source_amplitude", 0.0))
     return s
 
 
@@ -216,3 +223,12 @@ def sincos_turns(t):
     c = ctypes.c_double()
     lib().orc_sincos_turns(float(t), ctypes.byref(s), ctypes.byref(c))
     return s.value, c.value
+
+
+def apply_boundaries(prob, c2, f, fnew, t):
+    """Driven-wall boundary step on post-collision values (in place copy)."""
+    s = _struct(prob)
+    out = np.ascontiguousarray(fnew, dtype=np.float64).copy()
+    lib().orc_apply_boundaries(ctypes.byref(s), _p(np.ascontiguousarray(c2)),
+                               _p(np.ascontiguousarray(f, dtype=np.float64)), _p(out), int(t))
+    return out

@@ -56,9 +56,13 @@ typedef struct {
     int n_surface;         /* number of surface elements N                       */
     long n_steps;          /* total LB steps                                     */
     long n_window;         /* the last n_window steps are averaged               */
+    int driven;            /* 0: periodic box with the standing wave as initial
+                              state; 1: driven walls along wave_axis (Sec. VII) */
+    double wall_damping;   /* Phi of Eq. (73)                                    */
+    double source_amplitude; /* rho_a of the source sheet                        */
 } orc_problem;
 
-enum { ORC_FLUID = 0, ORC_OBJECT = 1, ORC_BAND = 2 };
+enum { ORC_FLUID = 0, ORC_OBJECT = 1, ORC_BAND = 2, ORC_WALL_LO = 3, ORC_WALL_HI = 4, ORC_SOURCE = 5 };
 
 int orc_threads(void)
 {
@@ -157,6 +161,13 @@ void orc_mask(const orc_problem *P, unsigned char *mask)
                 unsigned char c = ORC_BAND;
                 if (q >= half) c = ORC_FLUID;
                 else if (q <= -half) c = ORC_OBJECT;
+                if (P->driven) {
+                    int cc[3] = {x, y, z};
+                    int sa = cc[P->wave_axis], ns = P->n[P->wave_axis];
+                    if (sa == 0) c = ORC_WALL_LO;
+                    else if (sa == ns - 1) c = ORC_WALL_HI;
+                    else if (sa == 1) c = ORC_SOURCE;
+                }
                 mask[cell_index(P, x, y, z)] = c;
             }
 }
@@ -289,7 +300,7 @@ void orc_initial_populations(const orc_problem *P, const double *c2, double *f)
         for (int y = 0; y < P->n[1]; ++y)
             for (int x = 0; x < P->n[0]; ++x) {
                 size_t id = cell_index(P, x, y, z);
-                double rho = incident_pressure(P, x, y, z) / c2[id];
+                double rho = P->driven ? 0.0 : incident_pressure(P, x, y, z) / c2[id];
                 double feq[7];
                 equilibrium(P->dim, c2[id], rho, J0, feq);
                 for (int i = 0; i < Q; ++i) f[(size_t)i * cells + id] = feq[i];
@@ -343,6 +354,53 @@ void orc_collide(const orc_problem *P, const double *c2, const double *f, double
             fnew[k] = (1.0 - dt / tau) * f[k] + (dt / tau) * feq[i];
         }
     }
+}
+
+/* Driven-wall geometry of Sec. VII, applied to the post-collision values of
+ * step t (whose pre-collision populations are f):
+ *  - the two end planes along wave_axis are partially absorbing walls, where
+ *    a bounce-back step replaces the collision (Eq. 73): f_i^new = Phi f_j
+ *    with v_j = -v_i; the value that would leave the domain is dropped;
+ *  - the plane next to the low wall is the source sheet, where fields are
+ *    imposed after the collision (Eq. 72): f^new = f^eq(rho_a sin(w t), J1)
+ *    with J1 from Eq. (62) and w = 2 pi / T, T = lambda / c0 (t taken modulo T). */
+void orc_apply_boundaries(const orc_problem *P, const double *c2, const double *f, double *fnew, long t)
+{
+    if (!P->driven) return;
+    const double pi = 3.14159265358979323846264338327950288;
+    size_t cells = orc_cells(P);
+    int Q = orc_Q(P->dim), a = P->wave_axis, ns = P->n[a];
+    long T = (long)(P->wavelength / P->c0 + 0.5);
+    double rho_src = P->source_amplitude * sin(2.0 * pi * (double)(t % T) / (double)T);
+    for (int z = 0; z < P->n[2]; ++z)
+        for (int y = 0; y < P->n[1]; ++y)
+            for (int x = 0; x < P->n[0]; ++x) {
+                int cc[3] = {x, y, z};
+                int sa = cc[a];
+                if (sa != 0 && sa != 1 && sa != ns - 1) continue;
+                size_t id = cell_index(P, x, y, z);
+                double fi[7];
+                for (int i = 0; i < Q; ++i) fi[i] = f[(size_t)i * cells + id];
+                if (sa == 1) {
+                    double J[3] = {0.0, 0.0, 0.0};
+                    for (int i = 1; i < Q; ++i) {
+                        int v[3];
+                        velocity(i, v);
+                        for (int b = 0; b < P->dim; ++b) J[b] += v[b] * fi[i];
+                    }
+                    double feq[7];
+                    equilibrium(P->dim, c2[id], rho_src, J, feq);
+                    for (int i = 0; i < Q; ++i) fnew[(size_t)i * cells + id] = feq[i];
+                } else {
+                    for (int i = 0; i < Q; ++i) {
+                        int opp = i == 0 ? 0 : (((i - 1) % 2 == 0) ? i + 1 : i - 1);
+                        fnew[(size_t)i * cells + id] = P->wall_damping * fi[opp];
+                    }
+                    /* outward direction: -a at the low wall, +a at the high wall */
+                    int out = sa == 0 ? 2 + 2 * a : 1 + 2 * a;
+                    fnew[(size_t)out * cells + id] = 0.0;
+                }
+            }
 }
 
 /* Eq. (64): f_i(x + v_i) = f_i^new(x), periodic on every axis. */
@@ -459,6 +517,7 @@ int orc_run(const orc_problem *P, double F[3], double *p1_out, double *u1_out,
             }
         }
         orc_collide(P, c2, f, fnew);
+        orc_apply_boundaries(P, c2, f, fnew, t);
         orc_advect(P, fnew, f);
     }
     if (P->n_window > 0)

@@ -41,6 +41,8 @@ class Params(ctypes.Structure):
         ("n_surface", ctypes.c_int),
         ("n_periods", ctypes.c_int), ("n_avg_periods", ctypes.c_int),
         ("precision", ctypes.c_int),
+        ("boundary", ctypes.c_int),
+        ("wall_damping", ctypes.c_double), ("source_amplitude", ctypes.c_double),
     ]
 
 
@@ -52,6 +54,8 @@ class Info(ctypes.Structure):
         ("n_steps", ctypes.c_longlong), ("n_window", ctypes.c_longlong),
         ("steps_done", ctypes.c_longlong), ("samples_done", ctypes.c_longlong),
         ("bytes_per_update", ctypes.c_double), ("vector_path", ctypes.c_int),
+        ("steps_per_launch", ctypes.c_int),
+        ("two_step_rows", ctypes.c_int),
     ]
 
 
@@ -85,6 +89,7 @@ _SIGNATURES = {
     "wlb_surface": (ctypes.c_int, [_VP, _DP]),
     "wlb_mask": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ubyte)]),
     "wlb_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(Info)]),
+    "wlb_set_two_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "wlb_destroy": (ctypes.c_int, [_VP]),
     "wlb_average_noalloc": (ctypes.c_int, [_VP, ctypes.c_longlong, _DP]),
     "wlb_batch_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int,
@@ -158,6 +163,9 @@ def params_from_problem(prob, precision=None):
     p.n_avg_periods = int(prob["n_window"] // T)
     prec = precision or prob.get("precision", "f32")
     p.precision = {"f32": WLB_POP_F32, "f64": WLB_POP_F64, "f16": WLB_POP_F16}[prec]
+    p.boundary = 1 if prob.get("boundary", "periodic") == "driven" else 0
+    p.wall_damping = float(prob.get("wall_damping", 0.99))
+    p.source_amplitude = float(prob.get("source_amplitude", 0.0))
     return p
 
 
@@ -222,6 +230,10 @@ class Solver:
 
     def init(self):
         _check(lib().wlb_init(self._h), self._h, "wlb_init")
+
+    def set_two_step(self, enable=True, slab_rows=0):
+        """Unsampled steps two per launch (wlb_set_two_step)."""
+        _check(lib().wlb_set_two_step(self._h, 1 if enable else 0, int(slab_rows)), self._h, "wlb_set_two_step")
 
     def step(self, n, sample=False):
         _check(lib().wlb_step(self._h, int(n), 1 if sample else 0), self._h, "wlb_step")

@@ -72,6 +72,10 @@ Geometry make_geometry(const wlb_params *p) {
     g.surface_radius = p->surface_radius;
     g.band_half = 20.0 * p->interface_d;
     g.pop_scale = p->precision == WLB_POP_F16 ? 1.0 / p->p_a : 1.0;
+    g.driven = p->boundary == WLB_BOUNDARY_DRIVEN ? 1 : 0;
+    g.wall_damping = p->wall_damping;
+    g.source_amplitude = p->source_amplitude;
+    g.period = (long long)std::nearbyint(p->wavelength / p->c0);
     g.n_surface = p->n_surface;
     g.stencil = g.dim == 3 ? 27 : 9;
     return g;
@@ -130,11 +134,23 @@ void destroy_graphs(wlb_handle *h) {
     }
 }
 
+// Update launches in one period: each flips the population buffer.
+long long period_launches(const wlb_handle *h, bool sampled) {
+    return !sampled && h->two_step ? h->period / 2 + h->period % 2 : h->period;
+}
+
 // Issue one period of steps starting from buffer `start` on stream s.
 cudaError_t issue_period(wlb_handle *h, int start, bool sampled, cudaStream_t s) {
     int cur = start;
-    for (long long t = 0; t < h->period; ++t) {
-        cudaError_t e = wlb::launch_step(h->g, h->b, h->prec, cur, sampled, s);
+    long long t = 0;
+    if (!sampled && h->two_step)
+        for (; t + 1 < h->period; t += 2) {  // two steps per launch
+            cudaError_t e = wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, cur, h->b.err, s);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
+        }
+    for (; t < h->period; ++t) {  // graphs start on a period boundary
+        cudaError_t e = wlb::launch_step(h->g, h->b, h->prec, cur, sampled, t, s);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
@@ -196,7 +212,14 @@ wlb_status wlb_validate(const wlb_params *p) {
     if (p->precision == WLB_POP_F16 && !(p->p_a != 0.0)) return WLB_ERR_ARG;  // storage scale 1/p_a
     if (!(p->wavelength > 0) || !whole(p->wavelength / p->c0)) return WLB_ERR_ARG;
     const int n[3] = {p->nx, p->ny, p->nz};
-    if (!whole(n[p->wave_axis] / p->wavelength)) return WLB_ERR_ARG;
+    if (p->boundary != WLB_BOUNDARY_PERIODIC && p->boundary != WLB_BOUNDARY_DRIVEN) return WLB_ERR_ARG;
+    const bool driven = p->boundary == WLB_BOUNDARY_DRIVEN;
+    if (!driven && !whole(n[p->wave_axis] / p->wavelength)) return WLB_ERR_ARG;
+    if (driven) {
+        if (n[p->wave_axis] < 5) return WLB_ERR_ARG;
+        if (!(p->wall_damping >= 0.0 && p->wall_damping <= 1.0)) return WLB_ERR_ARG;
+        if (!std::isfinite(p->source_amplitude)) return WLB_ERR_ARG;
+    }
     if (!(p->radius > 0) || !(p->interface_d > 0) || !(p->surface_radius > 0)) return WLB_ERR_ARG;
     if (p->n_surface < 0 || p->n_periods < 1) return WLB_ERR_ARG;
     if (p->n_avg_periods < 0 || p->n_avg_periods > p->n_periods) return WLB_ERR_ARG;
@@ -207,6 +230,9 @@ wlb_status wlb_validate(const wlb_params *p) {
         if (!std::isfinite(p->center[a])) return WLB_ERR_ARG;
         if (2.0 * reach > n[a]) return WLB_ERR_ARG;
     }
+    // driven cavity: object, band and stencil clear of the walls and the source sheet
+    if (driven && (p->center[p->wave_axis] - reach < 2.0 || p->center[p->wave_axis] + reach > n[p->wave_axis] - 2.0))
+        return WLB_ERR_ARG;
     const double T = p->wavelength / p->c0;
     if ((double)p->n_periods * T > 9.0e15) return WLB_ERR_ARG;
     return WLB_OK;
@@ -263,6 +289,10 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
         wlb_destroy(h);
         return WLB_ERR_CUDA;
     }
+    // unsampled steps two per launch wherever the kernel applies (bit-identical)
+    if (wlb::two_step_supported(h->g, h->prec) && wlb::plan_two_steps(h->g, h->prec, 0, &h->two_plan) == cudaSuccess)
+        h->two_step = true;
+    cudaGetLastError();
     *out = h;
     return WLB_OK;
 }
@@ -283,18 +313,28 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
     DeviceGuard dg(h->device);
     const bool sampled = sample != 0 && h->g.n_surface > 0;
     while (n > 0) {
-        if (n >= h->period && (!sampled || h->samples_in_period == 0)) {
+        const bool aligned = !h->g.driven || h->steps_done % h->period == 0;  // source phase
+        if (n >= h->period && aligned && (!sampled || h->samples_in_period == 0)) {
             cudaGraphExec_t *slot = sampled ? &h->graph_sampled[h->src] : &h->graph_free[h->src];
             wlb_status st = period_graph(h, h->src, sampled, slot);
             if (st != WLB_OK) return st;
             WLB_CUDA(h, cudaGraphLaunch(*slot, h->stream), "graph launch");
-            if (h->period & 1) h->src ^= 1;
+            if (period_launches(h, sampled) & 1) h->src ^= 1;
             h->steps_done += h->period;
             if (sampled) h->samples_done += h->period;
             n -= h->period;
             continue;
         }
-        WLB_CUDA(h, wlb::launch_step(h->g, h->b, h->prec, h->src, sampled, h->stream), "step kernels");
+        if (!sampled && h->two_step && n >= 2) {
+            WLB_CUDA(h, wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, h->src, h->b.err, h->stream),
+                     "two-step kernel");
+            h->src ^= 1;
+            h->steps_done += 2;
+            n -= 2;
+            continue;
+        }
+        WLB_CUDA(h, wlb::launch_step(h->g, h->b, h->prec, h->src, sampled, h->steps_done % h->period, h->stream),
+                 "step kernels");
         h->src ^= 1;
         h->steps_done += 1;
         if (sampled) {
@@ -331,6 +371,7 @@ wlb_status wlb_force(wlb_handle *h, double force_out[3]) {
     int flag;
     memcpy(&flag, h->host_out + 4, sizeof(int));
     for (int i = 0; i < 3; ++i) force_out[i] = h->host_out[i];
+    if (flag == 2) return fail(h, WLB_ERR_TIMEOUT, "double-step plane wait limit reached");
     if (flag) return fail(h, WLB_ERR_UNSTABLE, "non-finite accumulators");
     return WLB_OK;
 }
@@ -387,6 +428,25 @@ wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out) {
     return WLB_OK;
 }
 
+wlb_status wlb_set_two_step(wlb_handle *h, int enable, int slab_rows) {
+    if (!h || slab_rows < 0) return WLB_ERR_ARG;
+    if (enable && !wlb::two_step_supported(h->g, h->prec))
+        return fail(h, WLB_ERR_ARG, "two steps per launch need a 3D periodic FP32/FP16 lattice of one-warp rows");
+    DeviceGuard dg(h->device);
+    wlb::TwoStepPlan plan;
+    if (enable) {
+        cudaError_t e = wlb::plan_two_steps(h->g, h->prec, slab_rows, &plan);
+        if (e != cudaSuccess) return fail(h, WLB_ERR_ARG, "slab height does not fit the shared memory", e);
+    }
+    const bool same = (enable != 0) == h->two_step && plan.H == h->two_plan.H && plan.zc == h->two_plan.zc;
+    if (!same) {
+        destroy_graphs(h);  // unsampled period graphs change shape
+        h->two_step = enable != 0;
+        h->two_plan = plan;
+    }
+    return WLB_OK;
+}
+
 wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out) {
     if (!h || !out) return WLB_ERR_ARG;
     out->dim = h->g.dim;
@@ -399,6 +459,8 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out) {
     out->samples_done = h->samples_done;
     out->bytes_per_update = 2.0 * h->g.q * (double)wlb::pop_bytes(h->prec) + 1.0;
     out->vector_path = h->vector_path ? 1 : 0;
+    out->steps_per_launch = h->two_step ? 2 : 1;
+    out->two_step_rows = h->two_step ? h->two_plan.H : 0;
     return WLB_OK;
 }
 

@@ -339,6 +339,7 @@ wlb_status batch_validate(const wlb_params *ps, int count) {
     for (int i = 0; i < count; ++i) {
         if (wlb_validate(&ps[i]) != WLB_OK) return WLB_ERR_ARG;
         if (ps[i].lattice != ps[0].lattice || ps[i].precision != ps[0].precision) return WLB_ERR_ARG;
+        if (ps[i].boundary != WLB_BOUNDARY_PERIODIC) return WLB_ERR_ARG;
         const int W = vec_width(wlb::prec_of(&ps[i]));
         if (ps[i].nx % W != 0 || ps[i].nx > 32 * W * wlb::kMaxChunks) return WLB_ERR_ARG;
     }

@@ -27,6 +27,8 @@ struct wlb_handle {
     cudaGraphExec_t graph_free[2] = {nullptr, nullptr};
     cudaGraphExec_t graph_sampled[2] = {nullptr, nullptr};
     bool vector_path = false;
+    bool two_step = false;      // unsampled steps two per launch (wlb_set_two_step)
+    wlb::TwoStepPlan two_plan;  // its grid, set by wlb_set_two_step
     char err[512] = {0};
 };
 

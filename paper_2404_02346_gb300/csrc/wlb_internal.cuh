@@ -7,7 +7,7 @@
 namespace wlb {
 
 // Cell classes (the byte field read by the update kernel).
-enum : uint8_t { CELL_FLUID = 0, CELL_OBJECT = 1, CELL_BAND = 2 };
+enum : uint8_t { CELL_FLUID = 0, CELL_OBJECT = 1, CELL_BAND = 2, CELL_WALL_LO = 3, CELL_WALL_HI = 4, CELL_SOURCE = 5 };
 
 // Population storage: FP32, FP64, or FP16 of f / p_a with FP32 arithmetic.
 enum class Prec { F32, F64, F16 };
@@ -29,6 +29,9 @@ struct Geometry {
     double radius, interface_d, surface_radius;
     double band_half;      // class threshold on |x-r0|^2 - R^2 (20 d)
     double pop_scale;      // stored populations are f * pop_scale (1, or 1/p_a for FP16)
+    int driven;            // 1: driven walls along wave_axis (Sec. VII)
+    double wall_damping, source_amplitude;
+    long long period;      // T = lambda / c0 steps
     int n_surface;
     int stencil;           // 3^dim
 };
@@ -53,16 +56,33 @@ struct Buffers {
 
 // Launchers (each TU owns its kernels).  All return cudaGetLastError().
 cudaError_t launch_setup(const Geometry &g, const Buffers &b, Prec p, cudaStream_t s);
-cudaError_t launch_update(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s,
+// t_mod: step index modulo the period (phase of the driven source).
+cudaError_t launch_update(const Geometry &g, const Buffers &b, Prec p, int src, long long t_mod, cudaStream_t s,
                           bool *vector_path);
 cudaError_t launch_sample(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s);
 // One whole step: the update, plus the surface sampling of the same input when
 // sample is set (fused into the update launch on the row-vectorised path).
-cudaError_t launch_step(const Geometry &g, const Buffers &b, Prec p, int src, bool sample, cudaStream_t s);
+cudaError_t launch_step(const Geometry &g, const Buffers &b, Prec p, int src, bool sample, long long t_mod,
+                        cudaStream_t s);
 cudaError_t launch_fold(const Geometry &g, const Buffers &b, Prec p, cudaStream_t s);
 cudaError_t launch_force(const Geometry &g, const Buffers &b, double n_window, cudaStream_t s);
 cudaError_t launch_fields(const Geometry &g, const Buffers &b, Prec p, int src,
                           long long first_cell, long long count, cudaStream_t s);
 bool update_is_vectorised(const Geometry &g, Prec p);
+
+// Two unsampled steps per launch (wlb_two_step.cu): 3D, periodic, FP32 or
+// FP16 rows of one warp (up to 8 values per lane).  Slab height H, slabs and
+// z-chunks of the grid, block size and dynamic shared memory.
+struct TwoStepPlan {
+    int H = 0, nslab = 0, chunks = 0, zc = 0, threads = 0;
+    size_t smem = 0;
+};
+bool two_step_supported(const Geometry &g, Prec p);
+// slab_rows: 0 picks H; otherwise that H.  Also opts the kernel into the
+// shared memory it needs on the current device.
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, TwoStepPlan *out);
+// From buffer src into src ^ 1.
+cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src, int *err,
+                             cudaStream_t s);
 
 }  // namespace wlb

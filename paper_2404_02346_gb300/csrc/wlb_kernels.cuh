@@ -24,6 +24,13 @@ template <> struct Store<float> {
     __device__ static void store(float *p, const float (&v)[4]) {
         __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
     }
+    __device__ static void store_keep(float *p, const float (&v)[4]) {  // normal L2 priority
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ static void load_cg(const float *p, float (&v)[4]) {  // L2 only (data written in this launch)
+        const float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
     __device__ static float get(const float *p) { return *p; }
     __device__ static void put(float *p, float v) { *p = v; }
 };
@@ -37,6 +44,13 @@ template <> struct Store<double> {
     }
     __device__ static void store(double *p, const double (&v)[2]) {
         __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+    }
+    __device__ static void store_keep(double *p, const double (&v)[2]) {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    }
+    __device__ static void load_cg(const double *p, double (&v)[2]) {
+        const double2 t = __ldcg(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x; v[1] = t.y;
     }
     __device__ static double get(const double *p) { return *p; }
     __device__ static void put(double *p, double v) { *p = v; }
@@ -65,6 +79,27 @@ template <> struct Store<__half> {
             memcpy(&w[i], &h, 4);
         }
         __stcs(reinterpret_cast<uint4 *>(p), make_uint4(w[0], w[1], w[2], w[3]));
+    }
+    __device__ static void store_keep(__half *p, const float (&v)[8]) {
+        unsigned w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+            memcpy(&w[i], &h, 4);
+        }
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __device__ static void load_cg(const __half *p, float (&v)[8]) {
+        const uint4 t = __ldcg(reinterpret_cast<const uint4 *>(p));
+        const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h;
+            memcpy(&h, &w[i], 4);
+            const float2 f = __half22float2(h);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
     }
     __device__ static float get(const __half *p) { return __half2float(*p); }
     __device__ static void put(__half *p, float v) { *p = __float2half_rn(v); }
@@ -105,6 +140,42 @@ __device__ __forceinline__ void pulled_moments(const Geometry &g, const S *__res
         const R fmz = Store<S>::get(src + 6 * nc + ((long long)zp * ny + y) * nx + x);
         rho += fpz + fmz;
         J[2] = fpz - fmz;
+    }
+}
+
+// Driven-cavity parameters of one step (Sec. VII).
+template <typename R>
+struct Drive {
+    R rho_src;  // imposed rho1 on the source sheet at this step
+    R phi;      // wall damping
+    int axis;   // wave axis
+};
+
+// Wall and source cells (classes >= CELL_WALL_LO) replace the collision:
+//   walls, Eq. (73): f*_i = Phi f_j, v_j = -v_i; the outward value is dropped;
+//   source, Eq. (72): f* = f^eq(rho_src, J1), J1 from the arrived populations.
+// fin / fout in velocity order (0, +x, -x, +y, -y, +z, -z).
+template <typename R, int Q>
+__device__ __forceinline__ void boundary_cell(unsigned k, const R (&fin)[Q], R c2, const Drive<R> &d,
+                                              R (&fout)[Q]) {
+    constexpr int D = (Q - 1) / 2;
+    if (k == CELL_SOURCE) {
+        const R eq = c2 * d.rho_src;
+        fout[0] = d.rho_src * (R(1) - R(D) * c2);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const R J = fin[1 + 2 * a] - fin[2 + 2 * a];
+            fout[1 + 2 * a] = R(0.5) * (eq + J);
+            fout[2 + 2 * a] = R(0.5) * (eq - J);
+        }
+    } else {
+        const int out = k == CELL_WALL_LO ? 2 + 2 * d.axis : 1 + 2 * d.axis;
+        fout[0] = d.phi * fin[0];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            fout[1 + 2 * a] = 1 + 2 * a == out ? R(0) : d.phi * fin[2 + 2 * a];
+            fout[2 + 2 * a] = 2 + 2 * a == out ? R(0) : d.phi * fin[1 + 2 * a];
+        }
     }
 }
 

@@ -86,7 +86,8 @@ extern "C" wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, doub
         long long in_period = 0;
         for (long long t = 0; t < n_steps && st == WLB_OK; ++t) {
             if ((e = wlb::launch_sample(h->g, b, h->prec, h->src, h->stream)) != cudaSuccess ||
-                (e = wlb::launch_update(h->g, b, h->prec, h->src, h->stream, nullptr)) != cudaSuccess) {
+                (e = wlb::launch_update(h->g, b, h->prec, h->src, h->steps_done % h->period, h->stream,
+                                        nullptr)) != cudaSuccess) {
                 st = note(h, WLB_ERR_CUDA, "step kernels", e);
                 break;
             }

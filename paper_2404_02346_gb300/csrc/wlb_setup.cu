@@ -79,19 +79,26 @@ __global__ void setup_cells(Geometry g, S *__restrict__ pop, uint8_t *__restrict
     int y = (int)(r % g.n[1]);
     int z = (int)(r / g.n[1]);
     double q = excess_r2(g, x, y, z);
-    cls[id] = cell_class(g, q);
-    double c2 = sound_speed_sq(g, x, y, z);
-    c2f[id] = (T)c2;
     const int cc[3] = {x, y, z};
     const int ax = g.wave_axis;
-    double p = ptab[cc[ax]];
+    uint8_t k = cell_class(g, q);
+    if (g.driven) {
+        const int sa = cc[ax], ns = g.n[ax];
+        if (sa == 0) k = CELL_WALL_LO;
+        else if (sa == ns - 1) k = CELL_WALL_HI;
+        else if (sa == 1) k = CELL_SOURCE;
+    }
+    cls[id] = k;
+    double c2 = sound_speed_sq(g, x, y, z);  // walls and source sheet lie in the fluid
+    c2f[id] = (T)c2;
+    double p = g.driven ? 0.0 : ptab[cc[ax]];  // the driven cavity starts from rest
     pop[id] = to_store<S>((p / c2) * (1.0 - g.dim * c2) * g.pop_scale);  // f_0^eq = rho1 (1 - D c^2)
     for (int i = 1; i < g.q; ++i) {
         int a = (i - 1) >> 1;
         int v = ((i - 1) & 1) ? -1 : 1;
         int c[3] = {x, y, z};
         c[a] = wrap_index(c[a] + v, g.n[a]);
-        double pn = ptab[c[ax]];
+        double pn = g.driven ? 0.0 : ptab[c[ax]];
         pop[(long long)i * g.ncell + id] = to_store<S>(0.5 * pn * g.pop_scale);  // f_i^eq = c^2 rho1 / 2
     }
 }

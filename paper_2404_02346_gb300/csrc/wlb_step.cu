@@ -16,6 +16,8 @@
 //     f*_-a = c^2 rho1 - J_a - f_-a = c^2 rho1 - f_+a.
 // The update is linear in f, so populations may be stored scaled (FP16 stores
 // f / p_a); the scale only enters the setup, the fold and the read-back.
+#include <cmath>
+
 #include "wlb_kernels.cuh"
 
 namespace wlb {
@@ -86,13 +88,14 @@ __global__ void __launch_bounds__(256) sample_points(SampleArgs<S> a, const S *_
 // the sampled step is one launch.  Launched with programmatic dependent
 // launch: every block lets the next launch start, then waits for the previous
 // one to finish before reading.
-template <typename S, int D, int CH>
+template <typename S, int D, int CH, bool DRIVEN>
 __global__ void __launch_bounds__(256) update_rows(const S *__restrict__ src, S *__restrict__ dst,
                                                    const uint8_t *__restrict__ cls,
                                                    const typename Store<S>::R *__restrict__ c2f, int nx,
                                                    int ny, int nz, long long ncell,
                                                    typename Store<S>::R c0sq, typename Store<S>::R cpsq,
-                                                   long long row_blocks, SampleArgs<S> sa) {
+                                                   long long row_blocks, SampleArgs<S> sa,
+                                                   Drive<typename Store<S>::R> drv) {
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
     constexpr int Q = 2 * D + 1;
@@ -174,6 +177,21 @@ __global__ void __launch_bounds__(256) update_rows(const S *__restrict__ src, S 
                 o[5][e] = eq - f[6][c][e];
                 o[6][e] = eq - f[5][c][e];
             }
+            if (DRIVEN && k >= CELL_WALL_LO) {  // driven cavity only
+                R fin[Q], fo[Q];
+                fin[0] = f[0][c][e];
+                fin[1] = fpx[e];
+                fin[2] = fmx[e];
+                fin[3] = f[3][c][e];
+                fin[4] = f[4][c][e];
+                if (D == 3) {
+                    fin[5] = f[5][c][e];
+                    fin[6] = f[6][c][e];
+                }
+                boundary_cell<R, Q>(k, fin, c2, drv, fo);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) o[i][e] = fo[i];
+            }
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) Store<S>::store(dst + i * ncell + r0 + x0, o[i]);
@@ -181,13 +199,15 @@ __global__ void __launch_bounds__(256) update_rows(const S *__restrict__ src, S 
 }
 
 // Any lattice shape: one thread per cell, scalar accesses.
-template <typename S, int D>
+template <typename S, int D, bool DRIVEN>
 __global__ void __launch_bounds__(256) update_cells(const S *__restrict__ src, S *__restrict__ dst,
                                                     const uint8_t *__restrict__ cls,
                                                     const typename Store<S>::R *__restrict__ c2f, int nx,
                                                     int ny, int nz, long long ncell,
-                                                    typename Store<S>::R c0sq, typename Store<S>::R cpsq) {
+                                                    typename Store<S>::R c0sq, typename Store<S>::R cpsq,
+                                                    Drive<typename Store<S>::R> drv) {
     using R = typename Store<S>::R;
+    constexpr int Q = 2 * D + 1;
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= ncell) return;
     const int x = (int)(id % nx);
@@ -213,15 +233,25 @@ __global__ void __launch_bounds__(256) update_cells(const S *__restrict__ src, S
     R rho = f0 + fpx + fmx + fpy + fmy;
     if (D == 3) rho += fpz + fmz;
     const R eq = c2 * rho;
-    Store<S>::put(dst + id, R(2) * (rho - R(D) * eq) - f0);
-    Store<S>::put(dst + ncell + id, eq - fmx);
-    Store<S>::put(dst + 2 * ncell + id, eq - fpx);
-    Store<S>::put(dst + 3 * ncell + id, eq - fmy);
-    Store<S>::put(dst + 4 * ncell + id, eq - fpy);
-    if (D == 3) {
-        Store<S>::put(dst + 5 * ncell + id, eq - fmz);
-        Store<S>::put(dst + 6 * ncell + id, eq - fpz);
+    R o[7];
+    o[0] = R(2) * (rho - R(D) * eq) - f0;
+    o[1] = eq - fmx;
+    o[2] = eq - fpx;
+    o[3] = eq - fmy;
+    o[4] = eq - fpy;
+    o[5] = eq - fmz;
+    o[6] = eq - fpz;
+    if (DRIVEN && k >= CELL_WALL_LO) {  // driven cavity only
+        R fin[Q], fo[Q];
+        const R all[7] = {f0, fpx, fmx, fpy, fmy, fpz, fmz};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fin[i] = all[i];
+        boundary_cell<R, Q>(k, fin, c2, drv, fo);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) o[i] = fo[i];
     }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Store<S>::put(dst + i * ncell + id, o[i]);
 }
 
 // acc64 += acc * scale (scale = 1 / pop_scale^2 converts stored units back).
@@ -304,8 +334,19 @@ SampleArgs<S> sample_args(const Geometry &g, const Buffers &b) {
 
 // Update launch (rows, plus sampling blocks when sample is set) with the
 // programmatic-serialization attribute.
+template <typename R>
+Drive<R> drive_of(const Geometry &g, long long t_mod) {
+    Drive<R> d;
+    const double two_pi = 6.283185307179586476925286766559;
+    d.rho_src = (R)(g.driven ? g.source_amplitude * std::sin(two_pi * (double)t_mod / (double)g.period) * g.pop_scale
+                             : 0.0);
+    d.phi = (R)g.wall_damping;
+    d.axis = g.wave_axis;
+    return d;
+}
+
 template <typename S, int D, int CH>
-cudaError_t run_rows(const Geometry &g, const Buffers &b, int src, bool sample, cudaStream_t s) {
+cudaError_t run_rows(const Geometry &g, const Buffers &b, int src, bool sample, long long t_mod, cudaStream_t s) {
     using R = typename Store<S>::R;
     const long long rows = (long long)g.n[1] * g.n[2];
     const long long row_blocks = (rows * 32 + 255) / 256;
@@ -319,9 +360,11 @@ cudaError_t run_rows(const Geometry &g, const Buffers &b, int src, bool sample, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, update_rows<S, D, CH>, (const S *)b.pop[src], (S *)b.pop[src ^ 1],
+    auto kern = g.driven ? update_rows<S, D, CH, true> : update_rows<S, D, CH, false>;
+    return cudaLaunchKernelEx(&cfg, kern, (const S *)b.pop[src], (S *)b.pop[src ^ 1],
                               (const uint8_t *)b.cls, (const R *)b.c2, g.n[0], g.n[1], g.n[2], g.ncell,
-                              (R)(g.c0 * g.c0), (R)(g.cp * g.cp), row_blocks, sample_args<S>(g, b));
+                              (R)(g.c0 * g.c0), (R)(g.cp * g.cp), row_blocks, sample_args<S>(g, b),
+                              drive_of<R>(g, t_mod));
 }
 
 template <typename S>
@@ -333,27 +376,31 @@ int row_chunks(const Geometry &g) {
 }
 
 template <typename S, int D>
-cudaError_t run_update(const Geometry &g, const Buffers &b, int src, bool sample, cudaStream_t s, bool *vec) {
+cudaError_t run_update(const Geometry &g, const Buffers &b, int src, bool sample, long long t_mod, cudaStream_t s,
+                       bool *vec) {
     using R = typename Store<S>::R;
     const int ch = row_chunks<S>(g);
     *vec = ch > 0;
     switch (ch) {
-        case 1: return run_rows<S, D, 1>(g, b, src, sample, s);
-        case 2: return run_rows<S, D, 2>(g, b, src, sample, s);
-        case 3: return run_rows<S, D, 3>(g, b, src, sample, s);
-        case 4: return run_rows<S, D, 4>(g, b, src, sample, s);
+        case 1: return run_rows<S, D, 1>(g, b, src, sample, t_mod, s);
+        case 2: return run_rows<S, D, 2>(g, b, src, sample, t_mod, s);
+        case 3: return run_rows<S, D, 3>(g, b, src, sample, t_mod, s);
+        case 4: return run_rows<S, D, 4>(g, b, src, sample, t_mod, s);
         default: break;
     }
     const long long blocks = (g.ncell + 255) / 256;
-    update_cells<S, D><<<(unsigned)blocks, 256, 0, s>>>(
+    auto kern = g.driven ? update_cells<S, D, true> : update_cells<S, D, false>;
+    kern<<<(unsigned)blocks, 256, 0, s>>>(
         (const S *)b.pop[src], (S *)b.pop[src ^ 1], b.cls, (const R *)b.c2, g.n[0], g.n[1], g.n[2],
-        g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp));
+        g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp), drive_of<R>(g, t_mod));
     return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t update_for(const Geometry &g, const Buffers &b, int src, bool sample, cudaStream_t s, bool *vec) {
-    return g.dim == 3 ? run_update<S, 3>(g, b, src, sample, s, vec) : run_update<S, 2>(g, b, src, sample, s, vec);
+cudaError_t update_for(const Geometry &g, const Buffers &b, int src, bool sample, long long t_mod, cudaStream_t s,
+                       bool *vec) {
+    return g.dim == 3 ? run_update<S, 3>(g, b, src, sample, t_mod, s, vec)
+                      : run_update<S, 2>(g, b, src, sample, t_mod, s, vec);
 }
 
 template <typename S>
@@ -383,29 +430,30 @@ bool update_is_vectorised(const Geometry &g, Prec p) {
     }
 }
 
-cudaError_t launch_update(const Geometry &g, const Buffers &b, Prec p, int src, cudaStream_t s,
+cudaError_t launch_update(const Geometry &g, const Buffers &b, Prec p, int src, long long t_mod, cudaStream_t s,
                           bool *vector_path) {
     bool vec = false;
     cudaError_t e;
     switch (p) {
-        case Prec::F64: e = update_for<double>(g, b, src, false, s, &vec); break;
-        case Prec::F16: e = update_for<__half>(g, b, src, false, s, &vec); break;
-        default: e = update_for<float>(g, b, src, false, s, &vec); break;
+        case Prec::F64: e = update_for<double>(g, b, src, false, t_mod, s, &vec); break;
+        case Prec::F16: e = update_for<__half>(g, b, src, false, t_mod, s, &vec); break;
+        default: e = update_for<float>(g, b, src, false, t_mod, s, &vec); break;
     }
     if (vector_path) *vector_path = vec;
     return e;
 }
 
-cudaError_t launch_step(const Geometry &g, const Buffers &b, Prec p, int src, bool sample, cudaStream_t s) {
+cudaError_t launch_step(const Geometry &g, const Buffers &b, Prec p, int src, bool sample, long long t_mod,
+                        cudaStream_t s) {
     if (!sample || g.n_surface == 0 || !update_is_vectorised(g, p)) {
         cudaError_t e = sample && g.n_surface > 0 ? launch_sample(g, b, p, src, s) : cudaSuccess;
-        return e == cudaSuccess ? launch_update(g, b, p, src, s, nullptr) : e;
+        return e == cudaSuccess ? launch_update(g, b, p, src, t_mod, s, nullptr) : e;
     }
     bool vec = false;
     switch (p) {
-        case Prec::F64: return update_for<double>(g, b, src, true, s, &vec);
-        case Prec::F16: return update_for<__half>(g, b, src, true, s, &vec);
-        default: return update_for<float>(g, b, src, true, s, &vec);
+        case Prec::F64: return update_for<double>(g, b, src, true, t_mod, s, &vec);
+        case Prec::F16: return update_for<__half>(g, b, src, true, t_mod, s, &vec);
+        default: return update_for<float>(g, b, src, true, t_mod, s, &vec);
     }
 }
 

@@ -1,0 +1,456 @@
+// Two lattice steps per launch (3D, periodic, unsampled steps): temporal
+// blocking in y-slabs with recomputed halo rows.
+//
+// The update is the fused advection + tau = 1/2 collision of update_rows
+// (Sec. V, Eqs. 62-64, 71) applied twice: S1 takes state t (buffer A) to t+1,
+// S2 takes t+1 to t+2 (buffer B).  State t+1 never leaves the SM.
+//
+// A CTA owns the H rows y0 .. y0+H-1 of the planes za .. zb-1 and sweeps z.
+// For each plane p = za-1 .. zb it computes S1 on the H + 2 rows y0-1 .. y0+H
+// (one halo row on either side, also computed by the neighbouring slab), then
+// S2 on plane p-1.  Warp w computes S1 on row y0-1+w and, for w = 1 .. H, S2 on
+// the same row, so S2 pulls
+//   rest, +x, -x   from the warp's registers of plane p-1 (x shift by shuffles),
+//   +z             from its registers of plane p-2,
+//   -z             from its registers of plane p,
+//   +y, -y         from rows w-1, w+1 of plane p-1, exchanged in shared memory
+//                  (a ring of three planes: one barrier per plane).
+// The A rows that S1 of a plane pulls from (seven populations x (H+2) rows)
+// and the rows of the c^2 field are staged in shared memory by 1-D bulk (TMA)
+// copies issued two planes ahead and completing on an mbarrier (two stages);
+// the field holds, for every cell, the c^2 the update uses (c0^2, cp^2, or
+// Eq. (79) in the band), so no warp waits on a global load of its own.  No CTA waits for another
+// CTA: one launch reads A and writes B once, about half the HBM traffic of two
+// single steps, plus the halo rows, which neighbouring slabs read at the same
+// time (L2 hits).  Results are bit-identical to two single steps: the same
+// per-cell arithmetic, and the t+1 values are rounded to the storage type as
+// a single step would store them.
+#include <algorithm>
+#include <cmath>
+
+#include "wlb_handle.cuh"
+#include "wlb_kernels.cuh"
+
+namespace wlb {
+namespace {
+
+constexpr long long kWaitLimit = 1LL << 22;  // mbarrier polls before giving up
+constexpr int kMaxRows = 16;                 // S1 rows (warps) per CTA
+constexpr int kRingPlanes = 3;               // +-y exchange ring
+constexpr int kStages = 2;                   // staged A planes
+
+// Threads per CTA: a warp per S1 row; rows with eight values per lane keep
+// enough registers (about 180) with at most eleven warps.
+template <typename S, int CH>
+constexpr int two_step_threads() {
+    return Store<S>::W * CH <= 4 ? 32 * kMaxRows : 32 * 11;
+}
+
+// Shared memory per S1 row: two staged planes of seven populations (storage
+// type) and of c^2 (arithmetic type), and the three-plane ring of the two
+// exchanged populations (storage type).
+constexpr size_t smem_per_row(size_t row_bytes, size_t c2_row_bytes) {
+    return (size_t)kStages * (7 * row_bytes + c2_row_bytes) + (size_t)kRingPlanes * 2 * row_bytes;
+}
+
+// W consecutive FP32 values from 16-byte aligned shared memory.
+template <int W>
+__device__ __forceinline__ void ld_f32(const float *p, float (&v)[W]) {
+#pragma unroll
+    for (int j = 0; j < W / 4; ++j) {
+        const float4 t = reinterpret_cast<const float4 *>(p)[j];
+        v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+    }
+}
+
+template <typename S> struct Vec;  // plain 16-byte shared-memory accesses
+
+template <> struct Vec<float> {
+    __device__ static void ld(const float *p, float (&v)[4]) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ static void st(float *p, const float (&v)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ static float rounded(float v) { return v; }
+};
+
+template <> struct Vec<__half> {
+    __device__ static void ld(const __half *p, float (&v)[8]) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(p);
+        const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h;
+            memcpy(&h, &w[i], 4);
+            const float2 f = __half22float2(h);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    }
+    __device__ static void st(__half *p, const float (&v)[8]) {
+        unsigned w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+            memcpy(&w[i], &h, 4);
+        }
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    // the value a single step would store and the next step read back
+    __device__ static float rounded(float v) { return __half2float(__float2half_rn(v)); }
+};
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a stage: false if it did not complete within the limit.
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (bar_try(bar, parity)) return true;
+    return false;
+}
+
+// 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(saddr(dst)),
+        "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(saddr(bar))
+        : "memory");
+}
+
+// Eq. (71) with tau = 1/2 in the form of update_rows: f* = 2 f^eq - f with the
+// pulled populations (0, +x, -x, +y, -y, +z, -z); same operation order.
+template <typename R>
+__device__ __forceinline__ void collide7(R c2, R f0, R fpx, R fmx, R fpy, R fmy, R fpz, R fmz, R (&o)[7]) {
+    R rho = f0 + fpx + fmx + fpy + fmy;
+    rho += fpz + fmz;
+    const R eq = c2 * rho;
+    o[0] = R(2) * (rho - R(3) * eq) - f0;
+    o[1] = eq - fmx;
+    o[2] = eq - fpx;
+    o[3] = eq - fmy;
+    o[4] = eq - fpy;
+    o[5] = eq - fmz;
+    o[6] = eq - fpz;
+}
+
+// +x / -x pulls of a warp-wide row held as CH chunks of W values per lane
+// (x = (c * 32 + lane) * W + e): value from x - 1 and from x + 1, periodic.
+template <typename R, int CH, int W>
+__device__ __forceinline__ void shift_x(const R (&px)[CH][W], const R (&mx)[CH][W], int lane, R (&fpx)[CH][W],
+                                        R (&fmx)[CH][W]) {
+    R up[CH], dn[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        up[c] = __shfl_sync(kFull, px[c][W - 1], (lane + 31) & 31);
+        dn[c] = __shfl_sync(kFull, mx[c][0], (lane + 1) & 31);
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        fpx[c][0] = lane == 0 ? up[(c + CH - 1) % CH] : up[c];
+#pragma unroll
+        for (int e = 1; e < W; ++e) fpx[c][e] = px[c][e - 1];
+#pragma unroll
+        for (int e = 0; e < W - 1; ++e) fmx[c][e] = mx[c][e + 1];
+        fmx[c][W - 1] = lane == 31 ? dn[(c + 1) % CH] : dn[c];
+    }
+}
+
+template <typename S, int CH>
+__global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
+    update2_slab(const S *__restrict__ A, S *__restrict__ B, const typename Store<S>::R *__restrict__ c2f, int nx,
+                 int ny, int nz, long long ncell, int H, int nslab, int zc, int *err) {
+    using R = typename Store<S>::R;
+    constexpr int W = Store<S>::W;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int rmax = H + 2;
+    const size_t rowel = (size_t)nx;
+    S *stage = reinterpret_cast<S *>(smem);                                // [kStages][7][rmax][nx]
+    R *c2s = reinterpret_cast<R *>(stage + (size_t)kStages * 7 * rmax * rowel);  // [kStages][rmax][nx]
+    S *ring = reinterpret_cast<S *>(c2s + (size_t)kStages * rmax * rowel);     // [kRingPlanes][2][rmax][nx]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ring + (size_t)kRingPlanes * 2 * rmax * rowel);
+
+    const int slab = blockIdx.x % nslab, chunk = blockIdx.x / nslab;
+    const int y0 = slab * H;
+    const int hs = min(H, ny - y0);  // rows of this slab
+    const int rs = hs + 2;           // S1 rows
+    const int za = chunk * zc, zb = min(nz, za + zc);
+    if (za >= zb) return;            // whole block: empty chunk
+    const int L = zb - za + 2;       // S1 planes za-1 .. zb
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t row_bytes = (uint32_t)(nx * sizeof(S)), c2_bytes = (uint32_t)(nx * sizeof(R));
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) bar_init(&bar[s]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // Stage the rows of S1 plane index k (plane za-1+k) into stage k % 2:
+    // lane i < 8 of warp 0 copies population i (i = 7: c^2) for the rs rows,
+    // one bulk copy per run of rows that is contiguous in memory (two where
+    // the slab's halo wraps around y).
+    auto issue = [&](int k) {
+        const int p = (za - 1 + k + nz) % nz;
+        const int buf = k % kStages;
+        if (lane == 0) bar_expect(&bar[buf], (uint32_t)rs * (7u * row_bytes + c2_bytes));
+        __syncwarp();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage
+        if (lane < 8) {
+            const int i = lane;
+            const int dy = i == 3 ? -1 : (i == 4 ? 1 : 0);       // +y pulls from y-1, -y from y+1
+            const int pp = i == 5 ? (p + nz - 1) % nz : (i == 6 ? (p + 1) % nz : p);
+            const int ys = ((y0 - 1 + dy) % ny + ny) % ny;        // source row of S1 row 0
+            for (int r = 0; r < rs;) {
+                const int yr = (ys + r) % ny;
+                const int len = min(rs - r, ny - yr);
+                const long long row0 = (long long)pp * ny + yr;
+                if (i == 7)
+                    bulk_load(c2s + ((size_t)buf * rmax + r) * rowel, c2f + row0 * nx, (uint32_t)len * c2_bytes,
+                              &bar[buf]);
+                else
+                    bulk_load(stage + ((size_t)(buf * 7 + i) * rmax + r) * rowel, A + (long long)i * ncell + row0 * nx,
+                              (uint32_t)len * row_bytes, &bar[buf]);
+                r += len;
+            }
+        }
+    };
+    if (warp == 0) {
+        issue(0);
+        issue(1);
+    }
+
+    const bool s1_row = warp < rs;
+    const bool s2_row = warp >= 1 && warp <= hs;
+    const int y = (y0 - 1 + warp + ny) % ny;
+    // registers carried between planes (S1 results in storage precision)
+    R n0[CH][W], n1[CH][W], n2[CH][W];  // rest, +x, -x of plane p-1
+    R pz0[CH][W], pz1[CH][W];           // +z of planes p-2, p-1
+    R cq[CH][W];                        // c^2 of plane p-1
+    int failed = 0;
+    int k = 0;
+    for (; k < L; ++k) {
+        const int p = (za - 1 + k + nz) % nz;
+        const int buf = k % kStages;
+        const bool ok = bar_wait(&bar[buf], (uint32_t)((k / kStages) & 1));
+        R c0v[CH][W], c1v[CH][W], c2v[CH][W], c5v[CH][W], c6v[CH][W];
+        R cs[CH][W];
+        if (s1_row) {
+            const S *st = stage + ((size_t)buf * 7 * rmax + warp) * rowel;
+            const R *cst = c2s + ((size_t)buf * rmax + warp) * rowel;
+            R f[7][CH][W];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int x0 = (c * 32 + lane) * W;
+#pragma unroll
+                for (int i = 0; i < 7; ++i) Vec<S>::ld(st + (size_t)i * rmax * rowel + x0, f[i][c]);
+                ld_f32<W>(cst + x0, cs[c]);
+            }
+            R fpx[CH][W], fmx[CH][W];
+            shift_x<R, CH, W>(f[1], f[2], lane, fpx, fmx);
+            S *ry = ring + ((size_t)(k % kRingPlanes) * 2 * rmax + warp) * rowel;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int x0 = (c * 32 + lane) * W;
+                R oy[W], omy[W];
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    R o[7];
+                    collide7(cs[c][e], f[0][c][e], fpx[c][e], fmx[c][e], f[3][c][e], f[4][c][e], f[5][c][e],
+                             f[6][c][e], o);
+                    c0v[c][e] = Vec<S>::rounded(o[0]);
+                    c1v[c][e] = Vec<S>::rounded(o[1]);
+                    c2v[c][e] = Vec<S>::rounded(o[2]);
+                    oy[e] = o[3];
+                    omy[e] = o[4];
+                    c5v[c][e] = Vec<S>::rounded(o[5]);
+                    c6v[c][e] = Vec<S>::rounded(o[6]);
+                }
+                Vec<S>::st(ry + x0, oy);                        // +y of row w
+                Vec<S>::st(ry + (size_t)rmax * rowel + x0, omy);  // -y of row w
+            }
+        }
+        // stage `buf` consumed, ring plane k written; any failed wait ends the sweep
+        if (__syncthreads_or(!ok)) {
+            failed = 1;
+            break;
+        }
+        if (warp == 0 && k + 2 < L) issue(k + 2);
+        if (k >= 2 && s2_row) {
+            const int q = (p + nz - 1) % nz;
+            const long long r0 = ((long long)q * ny + y) * nx;
+            const S *ry = ring + (size_t)((k - 1) % kRingPlanes) * 2 * rmax * rowel;
+            R fpx[CH][W], fmx[CH][W];
+            shift_x<R, CH, W>(n1, n2, lane, fpx, fmx);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int x0 = (c * 32 + lane) * W;
+                R fpy[W], fmy[W];
+                Vec<S>::ld(ry + (size_t)(warp - 1) * rowel + x0, fpy);             // +y of row w-1
+                Vec<S>::ld(ry + (size_t)(rmax + warp + 1) * rowel + x0, fmy);      // -y of row w+1
+                R o[7][W];
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    R t[7];
+                    collide7(cq[c][e], n0[c][e], fpx[c][e], fmx[c][e], fpy[e], fmy[e], pz0[c][e], c6v[c][e], t);
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) o[i][e] = t[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 7; ++i) Store<S>::store(B + i * ncell + r0 + x0, o[i]);
+            }
+        }
+        if (s1_row) {
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    cq[c][e] = cs[c][e];
+                    n0[c][e] = c0v[c][e];
+                    n1[c][e] = c1v[c][e];
+                    n2[c][e] = c2v[c][e];
+                    pz0[c][e] = pz1[c][e];
+                    pz1[c][e] = c5v[c][e];
+                }
+            }
+        }
+    }
+    if (failed && threadIdx.x == 0) {
+        atomicExch(err, 2);  // reported as WLB_ERR_TIMEOUT
+        // let the copies still in flight (stages k and k+1) land before exit
+        for (int j = k; j < k + 2 && j < L; ++j) bar_wait(&bar[j % kStages], (uint32_t)((j / kStages) & 1));
+    }
+}
+
+template <typename S>
+int chunks_of(const Geometry &g) {
+    constexpr int W = Store<S>::W;
+    if (g.n[0] % (32 * W)) return 0;
+    const int ch = g.n[0] / (32 * W);
+    return (ch >= 1 && W * ch <= 8) ? ch : 0;
+}
+
+// Slab height H (rows <= smem and thread limits; `want` > 0 asks for one)
+// and the z-chunk count minimising the estimated time: waves x planes per CTA
+// x rows moved per plane (H + 2 read, H written), one CTA per SM.
+template <typename S, int CH>
+cudaError_t plan_ch(const Geometry &g, int want, TwoStepPlan *pl) {
+    int dev = 0, sms = 0, smem_max = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int ny = g.n[1], nz = g.n[2];
+    const size_t per_row = smem_per_row((size_t)g.n[0] * sizeof(S), (size_t)g.n[0] * sizeof(typename Store<S>::R));
+    const size_t fixed = kStages * sizeof(uint64_t) + 16;
+    int rows = (int)(((size_t)smem_max - fixed) / per_row);
+    rows = std::min(rows, two_step_threads<S, CH>() / 32);
+    if (rows < 3) return cudaErrorInvalidValue;
+    long long best = -1;
+    const int h_lo = want > 0 ? want : 1, h_hi = want > 0 ? want : rows - 2;
+    if (h_hi > rows - 2) return cudaErrorInvalidValue;
+    for (int H = h_lo; H <= h_hi; ++H) {
+        const int nslab = (ny + H - 1) / H;
+        for (int C = 1; C <= nz; ++C) {
+            const int zc = (nz + C - 1) / C;
+            const int used = (nz + zc - 1) / zc;
+            const long long waves = ((long long)nslab * used + sms - 1) / sms;
+            const long long cost = waves * (zc + 2) * (2LL * H + 2);
+            if (best < 0 || cost < best || (cost == best && H > pl->H)) {
+                best = cost;
+                pl->H = H;
+                pl->nslab = nslab;
+                pl->chunks = used;
+                pl->zc = zc;
+            }
+        }
+    }
+    pl->threads = 32 * (pl->H + 2);
+    pl->smem = per_row * (pl->H + 2) + fixed;
+    return cudaFuncSetAttribute(update2_slab<S, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
+}
+
+template <typename S>
+cudaError_t plan_for(const Geometry &g, int want, TwoStepPlan *pl) {
+    switch (chunks_of<S>(g)) {
+        case 1: return plan_ch<S, 1>(g, want, pl);
+        case 2:
+            if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, pl);
+            return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename S, int CH>
+cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, int *err, cudaStream_t s) {
+    using R = typename Store<S>::R;
+    update2_slab<S, CH><<<pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(
+        (const S *)b.pop[src], (S *)b.pop[src ^ 1], (const R *)b.c2, g.n[0], g.n[1], g.n[2], g.ncell, pl.H,
+        pl.nslab, pl.zc, err);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_for(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, int *err,
+                       cudaStream_t s) {
+    switch (chunks_of<S>(g)) {
+        case 1: return launch_ch<S, 1>(g, b, pl, src, err, s);
+        case 2:
+            if constexpr (Store<S>::W * 2 <= 8) return launch_ch<S, 2>(g, b, pl, src, err, s);
+            return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool two_step_supported(const Geometry &g, Prec p) {
+    if (g.dim != 3 || g.driven) return false;
+    switch (p) {
+        case Prec::F16: return chunks_of<__half>(g) > 0;
+        case Prec::F32: return chunks_of<float>(g) > 0;
+        default: return false;
+    }
+}
+
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, TwoStepPlan *out) {
+    TwoStepPlan pl;
+    if (!two_step_supported(g, p)) return cudaErrorInvalidValue;
+    cudaError_t e = p == Prec::F16 ? plan_for<__half>(g, slab_rows, &pl) : plan_for<float>(g, slab_rows, &pl);
+    if (e == cudaSuccess) *out = pl;
+    return e;
+}
+
+// Two unsampled steps from buffer src into src ^ 1.
+cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src, int *err,
+                             cudaStream_t s) {
+    if (!pl.H) return cudaErrorInvalidValue;
+    switch (p) {
+        case Prec::F16: return launch_for<__half>(g, b, pl, src, err, s);
+        case Prec::F32: return launch_for<float>(g, b, pl, src, err, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace wlb

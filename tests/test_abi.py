@@ -131,3 +131,21 @@ def test_batch_workspace_validation(wlb):
                              n_periods=2, n_avg_periods=1)
     assert L.wlb_batch_workspace_bytes(arr(wide), 1, ctypes.byref(nb)) == wlb.WLB_ERR_ARG
     assert L.wlb_batch_workspace_bytes(arr(a), 0, ctypes.byref(nb)) == wlb.WLB_ERR_ARG
+
+
+def test_driven_geometry_validation(wlb):
+    p = workloads.problem(2, (32, 35), 1, 64.0, 3.0, (16.0, 14.0), cp=0.375, n_surface=8,
+                          n_periods=2, n_avg_periods=1)
+    p.update(boundary="driven", wall_damping=0.99, source_amplitude=0.016)
+    assert wlb.validate(wlb.params_from_problem(p)) == wlb.WLB_OK   # box need not hold whole wavelengths
+    near_wall = dict(p, center=(16.0, 8.0, 0.0))
+    assert wlb.validate(wlb.params_from_problem(near_wall)) == wlb.WLB_ERR_ARG
+    bad_phi = dict(p, wall_damping=1.5)
+    assert wlb.validate(wlb.params_from_problem(bad_phi)) == wlb.WLB_ERR_ARG
+    q = wlb.params_from_problem(p)
+    q.boundary = 7
+    assert wlb.validate(q) == wlb.WLB_ERR_ARG
+    # batches are periodic only
+    nb = ctypes.c_size_t()
+    arr = (wlb.Params * 1)(wlb.params_from_problem(p))
+    assert wlb.lib().wlb_batch_workspace_bytes(arr, 1, ctypes.byref(nb)) == wlb.WLB_ERR_ARG

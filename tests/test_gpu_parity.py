@@ -259,3 +259,125 @@ def test_fp16_benchmark_lattice_force_and_scaling(wlb):
     assert abs(F16[2] - F32[2]) <= 1e-2 * abs(F32[2])
     F16b = _gpu_run(wlb, dict(prob, p_a=2 * prob["p_a"]), fields=False, precision="f16")["force"]
     assert np.array_equal(F16b, 4 * F16)
+
+
+
+# --- driven cavity of Sec. VII (walls, source sheet) --------------------------------
+
+@pytest.mark.parametrize("case", ["2d_f64_percell", "3d_f32_rows", "3d_f16_rows"])
+def test_driven_cavity_parity(wlb, case):
+    if case == "2d_f64_percell":
+        prob = workloads.problem(2, (32, 35), 1, 64.0, 3.0, (16.25, 14.0), cp=0.375, n_surface=48,
+                                 n_periods=8, n_avg_periods=3, precision="f64", surface_radius=4.0)
+        tol_p, tol_f = 1e-9, 1e-9
+    else:
+        prec = "f32" if case == "3d_f32_rows" else "f16"
+        nx = 128 if prec == "f32" else 256
+        prob = workloads.problem(3, (nx, 24, 41), 2, 64.0, 3.0, (nx / 2 + 0.25, 12.5, 16.0), cp=0.4,
+                                 n_surface=120, n_periods=6, n_avg_periods=2, precision=prec,
+                                 surface_radius=4.0)
+        tol_p, tol_f = (1e-4, 1e-3) if prec == "f32" else (0.1, 1e-2)
+    prob.update(boundary="driven", wall_damping=0.99, source_amplitude=1e-3 / 0.0625)
+    o = oracle.run(prob, fields=True)
+    g = _gpu_run(wlb, prob)
+    m = oracle.mask(prob)
+    assert set(np.unique(m)) >= {3, 4, 5}
+    assert g["info"].vector_path == (0 if case == "2d_f64_percell" else 1)
+    _compare(prob, g, o, p1_tol=tol_p, force_rtol=tol_f)
+
+
+def test_driven_cavity_steps_split_across_calls(wlb):
+    """The source phase follows the step index when steps are issued in pieces
+    (graphs are used only from period boundaries)."""
+    prob = workloads.problem(2, (128, 35), 1, 64.0, 3.0, (64.0, 14.0), cp=0.375, n_surface=48,
+                             n_periods=4, n_avg_periods=2, precision="f64", surface_radius=4.0)
+    prob.update(boundary="driven", wall_damping=0.99, source_amplitude=1e-3 / 0.0625)
+    o = oracle.run(prob, fields=True)
+    with wlb.Solver(prob) as s:
+        s.init()
+        s.step(100, sample=False)
+        s.step(412, sample=False)   # ends on a period boundary (2 x 256)
+        s.step(300, sample=True)
+        s.step(212, sample=True)
+        F = s.force()
+        p1, u1 = s.fields()
+        g = {"force": F, "mask": s.mask(), "points": s.surface(), "p1": p1, "u1": u1}
+    _compare(prob, g, o, p1_tol=1e-9, force_rtol=1e-9)
+
+
+
+# --- two unsampled steps per launch (slab temporal blocking) --------------------------
+
+def _two_step_outputs(wlb, prob, precision, settings, tail_steps=3):
+    """Force of the whole protocol, then `tail_steps` more unsampled steps
+    (direct launches: one two-step launch and one single step for 3) and the
+    fields, for each (enable, slab_rows) in settings."""
+    out = []
+    for enable, rows in settings:
+        with wlb.Solver(prob, precision=precision) as s:
+            s.set_two_step(bool(enable), rows)
+            if enable:
+                info = s.info()
+                assert info.steps_per_launch == 2
+                assert info.two_step_rows == (rows or info.two_step_rows) and info.two_step_rows > 0
+            F = s.run()
+            s.step(tail_steps)
+            p1, u1 = s.fields()
+            out.append((F, p1, u1))
+    return out
+
+
+@pytest.mark.parametrize("shape,lam,precision,rows", [
+    ((128, 48, 64), 32.0, "f32", (0, 1, 5, 14)),   # one chunk per lane; ragged slabs for 5 and 14
+    ((256, 24, 32), 16.0, "f32", (0, 3, 7, 8)),    # two chunks per lane
+    ((128, 37, 48), 16.0, "f32", (0, 4, 11)),      # odd ny: ragged slabs; uneven z chunks
+    ((256, 40, 32), 16.0, "f16", (0, 2, 9)),       # FP16 storage: t+1 rounded as stored
+])
+def test_two_step_is_bit_identical(wlb, shape, lam, precision, rows):
+    """Same per-cell arithmetic as two single steps: forces and fields equal bit
+    for bit, for several slab heights (ragged last slabs and z chunks)."""
+    prob = workloads.problem(3, shape, 2, lam, 3.0, (shape[0] / 2 + 0.25, shape[1] / 2 - 0.5, lam / 8),
+                             cp=0.42, n_surface=200, n_periods=6, n_avg_periods=2)
+    out = _two_step_outputs(wlb, prob, precision, [(0, 0)] + [(1, r) for r in rows])
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0])
+        assert np.array_equal(out[0][1], o[1])
+        assert np.array_equal(out[0][2], o[2])
+
+
+def test_two_step_benchmark_lattice(wlb):
+    """256^3 benchmark lattice, full protocol: identical force with and without,
+    FP32 and FP16 storage."""
+    for precision in ("f32", "f16"):
+        prob = workloads.sphere_3d(seed=1, precision=precision)
+        F = []
+        for enable in (False, True):
+            with wlb.Solver(prob) as s:
+                s.set_two_step(enable)
+                F.append(s.run())
+        assert np.array_equal(F[0], F[1]), precision
+
+
+def test_two_step_rejected_where_unsupported(wlb):
+    p2 = workloads.problem(2, (128, 64), 1, 32.0, 4.0, (64.0, 4.0), cp=0.375, n_surface=16,
+                           n_periods=2, n_avg_periods=1)
+    p3 = workloads.problem(3, (128, 32, 32), 2, 16.0, 3.0, (64.0, 16.0, 2.0), cp=0.42, n_surface=16,
+                           n_periods=2, n_avg_periods=1)
+    p3odd = workloads.problem(3, (96, 32, 32), 2, 16.0, 3.0, (48.0, 16.0, 2.0), cp=0.42, n_surface=16,
+                              n_periods=2, n_avg_periods=1)
+    for prob, precision in ((p2, "f32"), (p3, "f64"), (p3odd, "f32")):
+        with wlb.Solver(prob, precision=precision) as s:
+            assert s.info().steps_per_launch == 1  # default: single steps where unsupported
+            with pytest.raises(wlb.WlbError):
+                s.set_two_step(True)
+            assert s.info().steps_per_launch == 1
+            s.set_two_step(False)
+    with wlb.Solver(p3, precision="f32") as s:
+        assert s.info().steps_per_launch == 2  # default: on where supported
+        rows = s.info().two_step_rows
+        for bad in (15, 64):  # taller than the shared memory / thread limit allows
+            with pytest.raises(wlb.WlbError):
+                s.set_two_step(True, bad)
+            assert s.info().steps_per_launch == 2 and s.info().two_step_rows == rows  # unchanged
+        s.set_two_step(False)
+        assert s.info().steps_per_launch == 1 and s.info().two_step_rows == 0
