@@ -65,7 +65,8 @@ def _traffic(kernel_src_sha, steps_per_launch=1):
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
+            v = v.strip()
+            vals[k.strip()] = v.split("`")[1] if v.startswith("`") else (v.split() or [""])[0]
     if vals.get("kernel_source_sha256") != kernel_src_sha:
         return None
     try:
@@ -75,9 +76,12 @@ def _traffic(kernel_src_sha, steps_per_launch=1):
 
 
 def _kernel_sha(steps_per_launch=1):
-    name = "wlb_two_step.cu" if steps_per_launch == 2 else "wlb_step.cu"
-    src = os.path.join(ROOT, "paper_2404_02346_gb300", "csrc", name)
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()
+    """sha256 over the update kernel's source and the device header it includes."""
+    csrc = os.path.join(ROOT, "paper_2404_02346_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("wlb_two_step.cu" if steps_per_launch == 2 else "wlb_step.cu", "wlb_kernels.cuh"):
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()
 
 
 class ClockSampler:
@@ -283,10 +287,12 @@ def run_gpu(args, prob):
            "forces_per_s": e2e_steps / e2e_s, "force": [float(v) for v in Fe]}
 
     peaks = _peaks()
-    # algorithmic HBM bytes of one update launch: every population read and
-    # written once (a double-step launch keeps the intermediate state in L2),
-    # plus the class byte
-    bpu = info.bytes_per_update
+    # algorithmic HBM bytes per cell of one update launch: every population
+    # read and written once, plus the class byte (one step per launch) or the
+    # c^2 value (two steps per launch: the state between them stays on chip)
+    q = 7
+    pop_bytes = (info.bytes_per_update - 1) / (2 * q)
+    bpu = info.bytes_per_update if spl == 1 else 2 * q * pop_bytes + (8 if args.precision == "f64" else 4)
     achieved = bpu * cells / (k1_ms * 1e-3) / 1e9
     if peaks and "hbm_gbs" in peaks:
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"

@@ -133,8 +133,9 @@ typedef struct {
                                    2 q pop_bytes + 1 (class byte); pop_bytes is
                                    4, 8 or 2                                   */
     int vector_path;            /* 1 if the row-vectorised update kernel is used */
-    int steps_per_launch;       /* unsampled steps per update launch: 1, or 2
-                                   with wlb_set_two_step                        */
+    int steps_per_launch;       /* steps per update launch: 1, or 2 with
+                                   wlb_set_two_step (the default where it
+                                   applies)                                     */
     int two_step_rows;          /* slab height of the two-step kernel, 0 off    */
 } wlb_info;
 
@@ -337,20 +338,23 @@ wlb_status wlb_mlp_destroy(wlb_mlp *m);
 /* Sizes and counters of a handle. */
 wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
 
-/* Unsampled steps two per launch: the update of Eqs. (62)-(64), (71) applied
- * twice in one kernel, bit-identical to two single steps.  Each block owns a
- * slab of slab_rows rows (y) of a range of planes (z); it computes the first
- * step on its rows plus one halo row on either side and keeps that state on
- * the SM, so the populations cross HBM about once per two steps.  No block
- * waits for another.  Sampled steps stay single.  On by default (set up by
- * wlb_create with an automatic slab height) wherever it is supported.
- * Supported: 3D, periodic boundaries, FP32 rows of nx = 128 or 256 cells or
- * FP16 rows of nx = 256 (one warp per row); otherwise WLB_ERR_ARG.
- * enable: 0 off, nonzero on.  slab_rows: 0 lets the library choose (largest
- * slab the shared memory holds, chunking z to fill the SMs), else that height
- * (WLB_ERR_ARG if it does not fit).  A stalled staging copy (bounded wait)
- * makes wlb_force return WLB_ERR_TIMEOUT.  The paper has no counterpart: it
- * is a memory-traffic optimisation of the same update. */
+/* Steps two per launch: the update of Eqs. (62)-(64), (71) applied twice in
+ * one kernel, bit-identical to two single steps.  Each block owns a slab of
+ * slab_rows rows (y) of a range of planes (z); it computes the first step on
+ * its rows plus one halo row on either side and keeps that state on the SM,
+ * so the populations cross HBM about once per two steps.  No block waits for
+ * another.  In sampled steps a small kernel before it adds the surface sums
+ * of both steps (t from the stored state, t+1 recomputed from it by the same
+ * arithmetic), in the order two single steps add them.  On by default (set
+ * up by wlb_create with an automatic slab height) wherever it is supported:
+ * 3D, periodic boundaries, FP32 rows of nx = 128 or 256 cells or FP16 rows of
+ * nx = 256 (one warp per row).  Elsewhere, or with enable = 0, every step is
+ * one launch.  enable: 0 off, nonzero on (WLB_ERR_ARG if unsupported).
+ * slab_rows: 0 lets the library choose (largest slab the shared memory
+ * holds, z chunked to fill the SMs), else that height (WLB_ERR_ARG if it does
+ * not fit; the setting is then unchanged).  A stalled staging copy (bounded
+ * wait) makes wlb_force return WLB_ERR_TIMEOUT.  The paper has no counterpart:
+ * it is a memory-traffic optimisation of the same update. */
 wlb_status wlb_set_two_step(wlb_handle *h, int enable, int slab_rows);
 
 /* Release the handle, its graphs, streams and any memory it allocated. */

@@ -135,17 +135,17 @@ void destroy_graphs(wlb_handle *h) {
 }
 
 // Update launches in one period: each flips the population buffer.
-long long period_launches(const wlb_handle *h, bool sampled) {
-    return !sampled && h->two_step ? h->period / 2 + h->period % 2 : h->period;
+long long period_launches(const wlb_handle *h, bool) {
+    return h->two_step ? h->period / 2 + h->period % 2 : h->period;
 }
 
 // Issue one period of steps starting from buffer `start` on stream s.
 cudaError_t issue_period(wlb_handle *h, int start, bool sampled, cudaStream_t s) {
     int cur = start;
     long long t = 0;
-    if (!sampled && h->two_step)
+    if (h->two_step)
         for (; t + 1 < h->period; t += 2) {  // two steps per launch
-            cudaError_t e = wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, cur, h->b.err, s);
+            cudaError_t e = wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, cur, sampled, h->b.err, s);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -325,12 +325,20 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
             n -= h->period;
             continue;
         }
-        if (!sampled && h->two_step && n >= 2) {
-            WLB_CUDA(h, wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, h->src, h->b.err, h->stream),
-                     "two-step kernel");
+        if (h->two_step && n >= 2 && (!sampled || h->samples_in_period + 2 <= h->period)) {
+            WLB_CUDA(h, wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, h->src, sampled, h->b.err, h->stream),
+                     "two-step kernels");
             h->src ^= 1;
             h->steps_done += 2;
             n -= 2;
+            if (sampled) {
+                h->samples_done += 2;
+                h->samples_in_period += 2;
+                if (h->samples_in_period == h->period) {
+                    WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->prec, h->stream), "fold kernel");
+                    h->samples_in_period = 0;
+                }
+            }
             continue;
         }
         WLB_CUDA(h, wlb::launch_step(h->g, h->b, h->prec, h->src, sampled, h->steps_done % h->period, h->stream),

@@ -115,18 +115,15 @@ __device__ __forceinline__ void update_row(const S *__restrict__ src, S *__restr
         for (int e = 0; e < W; ++e) {
             const unsigned k = (unsigned)(cl[c] >> (8 * e)) & 0xffu;
             const R c2 = k == CELL_FLUID ? c0sq : (k == CELL_OBJECT ? cpsq : c2f[r0 + x0 + e]);
-            R rho = f[0][c][e] + fpx[e] + fmx[e] + f[3][c][e] + f[4][c][e];
-            if (D == 3) rho += f[5][c][e] + f[6][c][e];
-            const R eq = c2 * rho;
-            o[0][e] = R(2) * (rho - R(D) * eq) - f[0][c][e];
-            o[1][e] = eq - fmx[e];
-            o[2][e] = eq - fpx[e];
-            o[3][e] = eq - f[4][c][e];
-            o[4][e] = eq - f[3][c][e];
-            if (D == 3) {
-                o[5][e] = eq - f[6][c][e];
-                o[6][e] = eq - f[5][c][e];
-            }
+            R fin[Q], fo[Q];
+            fin[0] = f[0][c][e];
+            fin[1] = fpx[e];
+            fin[2] = fmx[e];
+#pragma unroll
+            for (int i = 3; i < Q; ++i) fin[i] = f[i][c][e];
+            collide_half<R, D>(c2, fin, fo);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) o[i][e] = fo[i];
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) Store<S>::store(dst + i * ncell + r0 + x0, o[i]);
@@ -209,14 +206,8 @@ __global__ void __launch_bounds__(256) batch_sample(const BatchLat *__restrict__
             u[2] += __shfl_xor_sync(kFull, u[2], m);
         }
         if (lane == 0) {
-            const R *nrm = (const R *)L.b.nrm;
-            const R un = u[0] * nrm[4 * k] + u[1] * nrm[4 * k + 1] + u[2] * nrm[4 * k + 2];
             R *a = (R *)L.b.acc + 5 * (long long)k;
-            a[0] += pv * pv;
-            a[1] += u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            a[2] += u[0] * un;
-            a[3] += u[1] * un;
-            a[4] += u[2] * un;
+            accumulate_point(a, pv, u, (const R *)L.b.nrm + 4 * (long long)k);
             if ((t - L.window_begin + 1) % L.period == 0) {
                 const double scale = 1.0 / (L.g.pop_scale * L.g.pop_scale);
                 double *a64 = L.b.acc64 + 5 * (long long)k;

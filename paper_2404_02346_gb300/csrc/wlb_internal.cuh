@@ -70,7 +70,7 @@ cudaError_t launch_fields(const Geometry &g, const Buffers &b, Prec p, int src,
                           long long first_cell, long long count, cudaStream_t s);
 bool update_is_vectorised(const Geometry &g, Prec p);
 
-// Two unsampled steps per launch (wlb_two_step.cu): 3D, periodic, FP32 or
+// Two steps per launch (wlb_two_step.cu): 3D, periodic, FP32 or
 // FP16 rows of one warp (up to 8 values per lane).  Slab height H, slabs and
 // z-chunks of the grid, block size and dynamic shared memory.
 struct TwoStepPlan {
@@ -81,8 +81,9 @@ bool two_step_supported(const Geometry &g, Prec p);
 // slab_rows: 0 picks H; otherwise that H.  Also opts the kernel into the
 // shared memory it needs on the current device.
 cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, TwoStepPlan *out);
-// From buffer src into src ^ 1.
-cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src, int *err,
-                             cudaStream_t s);
+// From buffer src into src ^ 1; with sample, the surface sums of both steps
+// are accumulated too (a sampling kernel before the update).
+cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src, bool sample,
+                             int *err, cudaStream_t s);
 
 }  // namespace wlb

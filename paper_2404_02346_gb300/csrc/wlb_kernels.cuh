@@ -105,6 +105,35 @@ template <> struct Store<__half> {
     __device__ static void put(__half *p, float v) { *p = __float2half_rn(v); }
 };
 
+// Correctly rounded arithmetic that the compiler never fuses into FMAs: every
+// kernel that applies the collision or adds the sampling sums gets the same
+// bits, whatever code surrounds it (one-step, two-step and recomputed paths).
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// tau = 1/2 collision of one cell (Eq. 71 with the moments of Eq. 62): with
+// f^eq_0 = rho1 (1 - D c^2) and f^eq_{+-a} = (c^2 rho1 +- J_a) / 2, f* = 2 f^eq - f
+// gives f*_0 = 2 (rho1 - D c^2 rho1) - f_0 and f*_{+-a} = c^2 rho1 - f_{-+a}.
+// f: the pulled populations in velocity order (0, +x, -x, +y, -y, +z, -z).
+template <typename R, int D>
+__device__ __forceinline__ void collide_half(R c2, const R (&f)[2 * D + 1], R (&o)[2 * D + 1]) {
+    R rho = add_rn(add_rn(add_rn(add_rn(f[0], f[1]), f[2]), f[3]), f[4]);
+    if constexpr (D == 3) rho = add_rn(rho, add_rn(f[5], f[6]));
+    const R eq = mul_rn(c2, rho);
+    o[0] = sub_rn(mul_rn(R(2), sub_rn(rho, mul_rn(R(D), eq))), f[0]);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        o[1 + 2 * a] = sub_rn(eq, f[2 + 2 * a]);
+        o[2 + 2 * a] = sub_rn(eq, f[1 + 2 * a]);
+    }
+}
+
 template <int W>
 __device__ __forceinline__ unsigned long long load_classes(const uint8_t *p) {
     if constexpr (W == 8) return *reinterpret_cast<const unsigned long long *>(p);
@@ -141,6 +170,68 @@ __device__ __forceinline__ void pulled_moments(const Geometry &g, const S *__res
         rho += fpz + fmz;
         J[2] = fpz - fmz;
     }
+}
+
+// Surface sampling.  One warp per surface element; lane l < 3^dim handles
+// stencil cell l.  P = sum_l delta_l c_l^2 rho1_l and U = sum_l delta_l J1_l /
+// rho0 (Eqs. 80-81), then acc += (P^2, U.U, U_x (U.n), U_y (U.n), U_z (U.n))
+// in stored units.  `moments(x, y, z, rho, J)` gives rho1 and J1 of a cell at
+// the sampled time.
+template <typename S>
+struct SampleArgs {
+    Geometry g;
+    const int4 *st_xyz;
+    const typename Store<S>::R *st_w, *nrm;
+    typename Store<S>::R *acc;
+};
+
+template <typename S>
+inline SampleArgs<S> sample_args(const Geometry &g, const Buffers &b) {
+    using R = typename Store<S>::R;
+    SampleArgs<S> a;
+    a.g = g;
+    a.st_xyz = b.st_xyz;
+    a.st_w = (const R *)b.st_w;
+    a.nrm = (const R *)b.nrm;
+    a.acc = (R *)b.acc;
+    return a;
+}
+
+// acc += (P^2, U.U, U_x (U.n), U_y (U.n), U_z (U.n)), explicit rounding.
+template <typename R>
+__device__ __forceinline__ void accumulate_point(R *acc, R p, const R (&u)[3], const R *n) {
+    const R un = fma_rn(u[2], n[2], fma_rn(u[1], n[1], mul_rn(u[0], n[0])));
+    acc[0] = fma_rn(p, p, acc[0]);
+    acc[1] = add_rn(acc[1], fma_rn(u[2], u[2], fma_rn(u[1], u[1], mul_rn(u[0], u[0]))));
+    acc[2] = fma_rn(u[0], un, acc[2]);
+    acc[3] = fma_rn(u[1], un, acc[3]);
+    acc[4] = fma_rn(u[2], un, acc[4]);
+}
+
+template <typename S, typename M>
+__device__ __forceinline__ void sample_point_with(const SampleArgs<S> &a, int k, int lane, M moments) {
+    using R = typename Store<S>::R;
+    const Geometry &g = a.g;
+    R p = R(0), u[3] = {R(0), R(0), R(0)};
+    if (lane < g.stencil) {
+        const long long o = (long long)k * g.stencil + lane;
+        const int4 c = a.st_xyz[o];
+        R rho, J[3];
+        moments(c.x, c.y, c.z, rho, J);
+        const R wp = a.st_w[2 * o], wu = a.st_w[2 * o + 1];
+        p = wp * rho;
+        u[0] = wu * J[0];
+        u[1] = wu * J[1];
+        u[2] = wu * J[2];
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        p += __shfl_xor_sync(kFull, p, m);
+        u[0] += __shfl_xor_sync(kFull, u[0], m);
+        u[1] += __shfl_xor_sync(kFull, u[1], m);
+        u[2] += __shfl_xor_sync(kFull, u[2], m);
+    }
+    if (lane == 0) accumulate_point(a.acc + 5 * (long long)k, p, u, a.nrm + 4 * (long long)k);
 }
 
 // Driven-cavity parameters of one step (Sec. VII).

@@ -23,50 +23,11 @@
 namespace wlb {
 namespace {
 
-// One warp per surface element; lane l < 3^dim handles stencil cell l.
-// P = sum_l delta_l c_l^2 rho1_l and U = sum_l delta_l J1_l / rho0 (Eqs. 80-81),
-// then acc += (P^2, U.U, U_x (U.n), U_y (U.n), U_z (U.n)) in stored units.
-template <typename S>
-struct SampleArgs {
-    Geometry g;
-    const int4 *st_xyz;
-    const typename Store<S>::R *st_w, *nrm;
-    typename Store<S>::R *acc;
-};
-
 template <typename S>
 __device__ __forceinline__ void sample_point(const SampleArgs<S> &a, const S *__restrict__ src, int k, int lane) {
-    using R = typename Store<S>::R;
-    const Geometry &g = a.g;
-    R p = R(0), u[3] = {R(0), R(0), R(0)};
-    if (lane < g.stencil) {
-        const long long o = (long long)k * g.stencil + lane;
-        const int4 c = a.st_xyz[o];
-        R rho, J[3];
-        pulled_moments(g, src, c.x, c.y, c.z, rho, J);
-        const R wp = a.st_w[2 * o], wu = a.st_w[2 * o + 1];
-        p = wp * rho;
-        u[0] = wu * J[0];
-        u[1] = wu * J[1];
-        u[2] = wu * J[2];
-    }
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        p += __shfl_xor_sync(kFull, p, m);
-        u[0] += __shfl_xor_sync(kFull, u[0], m);
-        u[1] += __shfl_xor_sync(kFull, u[1], m);
-        u[2] += __shfl_xor_sync(kFull, u[2], m);
-    }
-    if (lane == 0) {
-        const R nx = a.nrm[4 * k], ny = a.nrm[4 * k + 1], nz = a.nrm[4 * k + 2];
-        const R un = u[0] * nx + u[1] * ny + u[2] * nz;
-        R *acc = a.acc + 5 * (long long)k;
-        acc[0] += p * p;
-        acc[1] += u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        acc[2] += u[0] * un;
-        acc[3] += u[1] * un;
-        acc[4] += u[2] * un;
-    }
+    sample_point_with(a, k, lane, [&](int x, int y, int z, typename Store<S>::R &rho, typename Store<S>::R(&J)[3]) {
+        pulled_moments(a.g, src, x, y, z, rho, J);
+    });
 }
 
 template <typename S>
@@ -165,33 +126,16 @@ __global__ void __launch_bounds__(256) update_rows(const S *__restrict__ src, S 
         for (int e = 0; e < W; ++e) {
             const unsigned k = (unsigned)(cl[c] >> (8 * e)) & 0xffu;
             const R c2 = k == CELL_FLUID ? c0sq : (k == CELL_OBJECT ? cpsq : c2f[r0 + x0 + e]);
-            R rho = f[0][c][e] + fpx[e] + fmx[e] + f[3][c][e] + f[4][c][e];
-            if (D == 3) rho += f[5][c][e] + f[6][c][e];
-            const R eq = c2 * rho;
-            o[0][e] = R(2) * (rho - R(D) * eq) - f[0][c][e];
-            o[1][e] = eq - fmx[e];
-            o[2][e] = eq - fpx[e];
-            o[3][e] = eq - f[4][c][e];
-            o[4][e] = eq - f[3][c][e];
-            if (D == 3) {
-                o[5][e] = eq - f[6][c][e];
-                o[6][e] = eq - f[5][c][e];
-            }
-            if (DRIVEN && k >= CELL_WALL_LO) {  // driven cavity only
-                R fin[Q], fo[Q];
-                fin[0] = f[0][c][e];
-                fin[1] = fpx[e];
-                fin[2] = fmx[e];
-                fin[3] = f[3][c][e];
-                fin[4] = f[4][c][e];
-                if (D == 3) {
-                    fin[5] = f[5][c][e];
-                    fin[6] = f[6][c][e];
-                }
-                boundary_cell<R, Q>(k, fin, c2, drv, fo);
+            R fin[Q], fo[Q];
+            fin[0] = f[0][c][e];
+            fin[1] = fpx[e];
+            fin[2] = fmx[e];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) o[i][e] = fo[i];
-            }
+            for (int i = 3; i < Q; ++i) fin[i] = f[i][c][e];
+            collide_half<R, D>(c2, fin, fo);
+            if (DRIVEN && k >= CELL_WALL_LO) boundary_cell<R, Q>(k, fin, c2, drv, fo);  // driven cavity only
+#pragma unroll
+            for (int i = 0; i < Q; ++i) o[i][e] = fo[i];
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) Store<S>::store(dst + i * ncell + r0 + x0, o[i]);
@@ -230,26 +174,12 @@ __global__ void __launch_bounds__(256) update_cells(const S *__restrict__ src, S
     }
     const uint8_t k = cls[id];
     const R c2 = k == CELL_FLUID ? c0sq : (k == CELL_OBJECT ? cpsq : c2f[id]);
-    R rho = f0 + fpx + fmx + fpy + fmy;
-    if (D == 3) rho += fpz + fmz;
-    const R eq = c2 * rho;
-    R o[7];
-    o[0] = R(2) * (rho - R(D) * eq) - f0;
-    o[1] = eq - fmx;
-    o[2] = eq - fpx;
-    o[3] = eq - fmy;
-    o[4] = eq - fpy;
-    o[5] = eq - fmz;
-    o[6] = eq - fpz;
-    if (DRIVEN && k >= CELL_WALL_LO) {  // driven cavity only
-        R fin[Q], fo[Q];
-        const R all[7] = {f0, fpx, fmx, fpy, fmy, fpz, fmz};
+    const R all[7] = {f0, fpx, fmx, fpy, fmy, fpz, fmz};
+    R fin[Q], o[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) fin[i] = all[i];
-        boundary_cell<R, Q>(k, fin, c2, drv, fo);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) o[i] = fo[i];
-    }
+    for (int i = 0; i < Q; ++i) fin[i] = all[i];
+    collide_half<R, D>(c2, fin, o);
+    if (DRIVEN && k >= CELL_WALL_LO) boundary_cell<R, Q>(k, fin, c2, drv, o);  // driven cavity only
 #pragma unroll
     for (int i = 0; i < Q; ++i) Store<S>::put(dst + i * ncell + id, o[i]);
 }
@@ -320,17 +250,6 @@ __global__ void read_fields(Geometry g, const S *__restrict__ src, const uint8_t
     for (int a = 0; a < g.dim; ++a) stage[(long long)(1 + a) * count + j] = (double)J[a] * unscale / g.rho0;
 }
 
-template <typename S>
-SampleArgs<S> sample_args(const Geometry &g, const Buffers &b) {
-    using R = typename Store<S>::R;
-    SampleArgs<S> a;
-    a.g = g;
-    a.st_xyz = b.st_xyz;
-    a.st_w = (const R *)b.st_w;
-    a.nrm = (const R *)b.nrm;
-    a.acc = (R *)b.acc;
-    return a;
-}
 
 // Update launch (rows, plus sampling blocks when sample is set) with the
 // programmatic-serialization attribute.

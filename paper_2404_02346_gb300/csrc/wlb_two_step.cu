@@ -139,20 +139,12 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
-// Eq. (71) with tau = 1/2 in the form of update_rows: f* = 2 f^eq - f with the
-// pulled populations (0, +x, -x, +y, -y, +z, -z); same operation order.
+// The collision of the one-step kernels (collide_half), pulled populations
+// (0, +x, -x, +y, -y, +z, -z) passed one by one.
 template <typename R>
 __device__ __forceinline__ void collide7(R c2, R f0, R fpx, R fmx, R fpy, R fmy, R fpz, R fmz, R (&o)[7]) {
-    R rho = f0 + fpx + fmx + fpy + fmy;
-    rho += fpz + fmz;
-    const R eq = c2 * rho;
-    o[0] = R(2) * (rho - R(3) * eq) - f0;
-    o[1] = eq - fmx;
-    o[2] = eq - fpx;
-    o[3] = eq - fmy;
-    o[4] = eq - fpy;
-    o[5] = eq - fmz;
-    o[6] = eq - fpz;
+    const R f[7] = {f0, fpx, fmx, fpy, fmy, fpz, fmz};
+    collide_half<R, 3>(c2, f, o);
 }
 
 // +x / -x pulls of a warp-wide row held as CH chunks of W values per lane
@@ -175,6 +167,65 @@ __device__ __forceinline__ void shift_x(const R (&px)[CH][W], const R (&mx)[CH][
         for (int e = 0; e < W - 1; ++e) fmx[c][e] = mx[c][e + 1];
         fmx[c][W - 1] = lane == 31 ? dn[(c + 1) % CH] : dn[c];
     }
+}
+
+// rho1 and J1 of cell (x, y, z) at t+1 from the populations A of time t.
+// Each of the seven values the cell pulls is the t+1 post-collision value of
+// the neighbour it comes from, recomputed from A with the arithmetic of the
+// update and rounded to the storage type as a single step stores it; they are
+// then summed in the order of pulled_moments, so sampling t+1 here gives the
+// same bits as sampling the stored state t+1.
+template <typename S>
+__device__ __forceinline__ void moments_next(const Geometry &g, const S *__restrict__ A,
+                                             const typename Store<S>::R *__restrict__ c2f, int x, int y, int z,
+                                             typename Store<S>::R &rho, typename Store<S>::R (&J)[3]) {
+    using R = typename Store<S>::R;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long nc = g.ncell;
+    auto dn = [](int v, int n) { return v == 0 ? n - 1 : v - 1; };
+    auto up = [](int v, int n) { return v == n - 1 ? 0 : v + 1; };
+    auto post = [&](int i, int cx, int cy, int cz) -> R {  // f*_i(cx, cy, cz) at t+1
+        const long long row = ((long long)cz * ny + cy) * nx;
+        const R f0 = Store<S>::get(A + row + cx);
+        const R fpx = Store<S>::get(A + nc + row + dn(cx, nx));
+        const R fmx = Store<S>::get(A + 2 * nc + row + up(cx, nx));
+        const R fpy = Store<S>::get(A + 3 * nc + ((long long)cz * ny + dn(cy, ny)) * nx + cx);
+        const R fmy = Store<S>::get(A + 4 * nc + ((long long)cz * ny + up(cy, ny)) * nx + cx);
+        const R fpz = Store<S>::get(A + 5 * nc + ((long long)dn(cz, nz) * ny + cy) * nx + cx);
+        const R fmz = Store<S>::get(A + 6 * nc + ((long long)up(cz, nz) * ny + cy) * nx + cx);
+        R o[7];
+        collide7(c2f[row + cx], f0, fpx, fmx, fpy, fmy, fpz, fmz, o);
+        return Vec<S>::rounded(o[i]);
+    };
+    const R f0 = post(0, x, y, z);
+    const R fpx = post(1, dn(x, nx), y, z);
+    const R fmx = post(2, up(x, nx), y, z);
+    const R fpy = post(3, x, dn(y, ny), z);
+    const R fmy = post(4, x, up(y, ny), z);
+    const R fpz = post(5, x, y, dn(z, nz));
+    const R fmz = post(6, x, y, up(z, nz));
+    rho = f0 + fpx + fmx + fpy + fmy;
+    J[0] = fpx - fmx;
+    J[1] = fpy - fmy;
+    rho += fpz + fmz;
+    J[2] = fpz - fmz;
+}
+
+// Surface sums of the two steps of a launch (times t and t+1), in the order
+// two single steps add them; reads only A, before the two-step kernel runs.
+template <typename S>
+__global__ void __launch_bounds__(256) sample_two(SampleArgs<S> a, const S *__restrict__ A,
+                                                  const typename Store<S>::R *__restrict__ c2f) {
+    using R = typename Store<S>::R;
+    const int lane = threadIdx.x & 31;
+    const int k = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (k >= a.g.n_surface) return;  // uniform per warp
+    sample_point_with(a, k, lane, [&](int x, int y, int z, R &rho, R(&J)[3]) {
+        pulled_moments(a.g, A, x, y, z, rho, J);
+    });
+    sample_point_with(a, k, lane, [&](int x, int y, int z, R &rho, R(&J)[3]) {
+        moments_next(a.g, A, c2f, x, y, z, rho, J);
+    });
 }
 
 template <typename S, int CH>
@@ -353,7 +404,10 @@ int chunks_of(const Geometry &g) {
 
 // Slab height H (rows <= smem and thread limits; `want` > 0 asks for one)
 // and the z-chunk count minimising the estimated time: waves x planes per CTA
-// x rows moved per plane (H + 2 read, H written), one CTA per SM.
+// x rows moved per plane (H + 2 read, H written), one CTA per SM.  Among
+// heights within 5 % of the best estimate the tallest is taken: each plane
+// costs a CTA a fixed latency besides its bytes, so fewer, taller slabs win
+// where the bytes alone do not decide.
 template <typename S, int CH>
 cudaError_t plan_ch(const Geometry &g, int want, TwoStepPlan *pl) {
     int dev = 0, sms = 0, smem_max = 0;
@@ -367,25 +421,33 @@ cudaError_t plan_ch(const Geometry &g, int want, TwoStepPlan *pl) {
     int rows = (int)(((size_t)smem_max - fixed) / per_row);
     rows = std::min(rows, two_step_threads<S, CH>() / 32);
     if (rows < 3) return cudaErrorInvalidValue;
-    long long best = -1;
     const int h_lo = want > 0 ? want : 1, h_hi = want > 0 ? want : rows - 2;
     if (h_hi > rows - 2) return cudaErrorInvalidValue;
+    TwoStepPlan per_h[kMaxRows];
+    long long cost_h[kMaxRows], best = -1;
     for (int H = h_lo; H <= h_hi; ++H) {
         const int nslab = (ny + H - 1) / H;
+        cost_h[H] = -1;
         for (int C = 1; C <= nz; ++C) {
             const int zc = (nz + C - 1) / C;
             const int used = (nz + zc - 1) / zc;
             const long long waves = ((long long)nslab * used + sms - 1) / sms;
             const long long cost = waves * (zc + 2) * (2LL * H + 2);
-            if (best < 0 || cost < best || (cost == best && H > pl->H)) {
-                best = cost;
-                pl->H = H;
-                pl->nslab = nslab;
-                pl->chunks = used;
-                pl->zc = zc;
+            if (cost_h[H] < 0 || cost < cost_h[H]) {
+                cost_h[H] = cost;
+                per_h[H].H = H;
+                per_h[H].nslab = nslab;
+                per_h[H].chunks = used;
+                per_h[H].zc = zc;
             }
         }
+        if (best < 0 || cost_h[H] < best) best = cost_h[H];
     }
+    for (int H = h_hi; H >= h_lo; --H)
+        if (cost_h[H] * 100 <= best * 105) {
+            *pl = per_h[H];
+            break;
+        }
     pl->threads = 32 * (pl->H + 2);
     pl->smem = per_row * (pl->H + 2) + fixed;
     return cudaFuncSetAttribute(update2_slab<S, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
@@ -403,8 +465,14 @@ cudaError_t plan_for(const Geometry &g, int want, TwoStepPlan *pl) {
 }
 
 template <typename S, int CH>
-cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, int *err, cudaStream_t s) {
+cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, bool sample, int *err,
+                      cudaStream_t s) {
     using R = typename Store<S>::R;
+    if (sample && g.n_surface > 0) {
+        const long long blocks = ((long long)g.n_surface * 32 + 255) / 256;
+        sample_two<S><<<(unsigned)blocks, 256, 0, s>>>(sample_args<S>(g, b), (const S *)b.pop[src],
+                                                       (const R *)b.c2);
+    }
     update2_slab<S, CH><<<pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(
         (const S *)b.pop[src], (S *)b.pop[src ^ 1], (const R *)b.c2, g.n[0], g.n[1], g.n[2], g.ncell, pl.H,
         pl.nslab, pl.zc, err);
@@ -412,12 +480,12 @@ cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl
 }
 
 template <typename S>
-cudaError_t launch_for(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, int *err,
+cudaError_t launch_for(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, bool sample, int *err,
                        cudaStream_t s) {
     switch (chunks_of<S>(g)) {
-        case 1: return launch_ch<S, 1>(g, b, pl, src, err, s);
+        case 1: return launch_ch<S, 1>(g, b, pl, src, sample, err, s);
         case 2:
-            if constexpr (Store<S>::W * 2 <= 8) return launch_ch<S, 2>(g, b, pl, src, err, s);
+            if constexpr (Store<S>::W * 2 <= 8) return launch_ch<S, 2>(g, b, pl, src, sample, err, s);
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
@@ -442,13 +510,13 @@ cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, TwoStepPlan
     return e;
 }
 
-// Two unsampled steps from buffer src into src ^ 1.
-cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src, int *err,
-                             cudaStream_t s) {
+// Two steps from buffer src into src ^ 1, sampling both when asked.
+cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src, bool sample,
+                             int *err, cudaStream_t s) {
     if (!pl.H) return cudaErrorInvalidValue;
     switch (p) {
-        case Prec::F16: return launch_for<__half>(g, b, pl, src, err, s);
-        case Prec::F32: return launch_for<float>(g, b, pl, src, err, s);
+        case Prec::F16: return launch_for<__half>(g, b, pl, src, sample, err, s);
+        case Prec::F32: return launch_for<float>(g, b, pl, src, sample, err, s);
         default: return cudaErrorInvalidValue;
     }
 }

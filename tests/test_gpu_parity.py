@@ -345,6 +345,26 @@ def test_two_step_is_bit_identical(wlb, shape, lam, precision, rows):
         assert np.array_equal(out[0][2], o[2])
 
 
+def test_two_step_odd_period_and_split_calls(wlb):
+    """Odd period T = 25 (a single step closes every period and a two-step
+    launch never crosses a fold) and sampled/unsampled calls of odd lengths:
+    force, sums and fields bit-identical to single steps."""
+    prob = workloads.problem(3, (128, 32, 25), 2, 6.25, 2.5, (64.25, 16.5, 3.0), cp=0.42, n_surface=120,
+                             n_periods=6, n_avg_periods=3)
+    out = []
+    for enable in (False, True):
+        with wlb.Solver(prob) as s:
+            s.set_two_step(enable)
+            s.init()
+            for n, smp in ((7, False), (68, False), (13, True), (1, True), (40, True), (3, True), (18, True)):
+                s.step(n, sample=smp)
+            F = s.force()
+            p1, u1 = s.fields()
+            out.append((F, p1, u1))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
 def test_two_step_benchmark_lattice(wlb):
     """256^3 benchmark lattice, full protocol: identical force with and without,
     FP32 and FP16 storage."""
