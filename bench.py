@@ -288,11 +288,10 @@ def run_gpu(args, prob):
 
     peaks = _peaks()
     # algorithmic HBM bytes per cell of one update launch: every population
-    # read and written once, plus the class byte (one step per launch) or the
-    # c^2 value (two steps per launch: the state between them stays on chip)
-    q = 7
-    pop_bytes = (info.bytes_per_update - 1) / (2 * q)
-    bpu = info.bytes_per_update if spl == 1 else 2 * q * pop_bytes + (8 if args.precision == "f64" else 4)
+    # read and written once, plus the class byte (also with two steps per
+    # launch: the state between them stays on chip; c^2 of the few
+    # interface-band rows is not counted)
+    bpu = info.bytes_per_update
     achieved = bpu * cells / (k1_ms * 1e-3) / 1e9
     if peaks and "hbm_gbs" in peaks:
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"

@@ -102,6 +102,7 @@ size_t layout(const Geometry &g, Prec prec, char *base, Buffers *b) {
     t.pop[0] = take(g.q * nc * P);
     t.pop[1] = take(g.q * nc * P);
     t.cls = (uint8_t *)take(nc);
+    t.band_rows = (uint8_t *)take((size_t)g.n[1] * g.n[2]);
     t.c2 = take(nc * T);
     t.pts = (double *)take(N * 7 * sizeof(double));
     t.st_xyz = (int4 *)take(N * S * sizeof(int4));

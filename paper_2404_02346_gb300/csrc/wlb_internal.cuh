@@ -40,6 +40,7 @@ struct Geometry {
 struct Buffers {
     void *pop[2];          // populations, q * ncell stored values each
     uint8_t *cls;          // ncell
+    uint8_t *band_rows;    // ny * nz: 1 where row (y, z) holds an interface-band cell
     void *c2;              // ncell reals: sound speed squared (read for band cells)
     double *pts;           // n_surface * 7
     int4 *st_xyz;          // n_surface * stencil: wrapped cell coordinates

@@ -70,7 +70,7 @@ template <> __device__ __forceinline__ __half to_store<__half>(double v) { retur
 // the equilibrium (Eq. 71 with rho1 = p1/c^2, J1 = 0) of the cell x + v_i,
 // times the storage scale.
 template <typename S, typename T>
-__global__ void setup_cells(Geometry g, S *__restrict__ pop, uint8_t *__restrict__ cls,
+__global__ void setup_cells(Geometry g, S *__restrict__ pop, uint8_t *__restrict__ cls, uint8_t *__restrict__ band_rows,
                             T *__restrict__ c2f, const double *__restrict__ ptab) {
     long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= g.ncell) return;
@@ -89,6 +89,7 @@ __global__ void setup_cells(Geometry g, S *__restrict__ pop, uint8_t *__restrict
         else if (sa == 1) k = CELL_SOURCE;
     }
     cls[id] = k;
+    if (k == CELL_BAND) band_rows[r] = 1;  // r = z * ny + y; every writer stores the same value
     double c2 = sound_speed_sq(g, x, y, z);  // walls and source sheet lie in the fluid
     c2f[id] = (T)c2;
     double p = g.driven ? 0.0 : ptab[cc[ax]];  // the driven cavity starts from rest
@@ -208,8 +209,10 @@ cudaError_t setup_impl(const Geometry &g, const Buffers &b, cudaStream_t s) {
     incident_table<<<(ns + 127) / 128, 128, 0, s>>>(g, b.ptab);
     cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
-    setup_cells<S, T><<<(unsigned)blocks, tb, 0, s>>>(g, (S *)b.pop[0], b.cls, (T *)b.c2, b.ptab);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(b.band_rows, 0, (size_t)g.n[1] * g.n[2], s);
+    if (e != cudaSuccess) return e;
+    setup_cells<S, T><<<(unsigned)blocks, tb, 0, s>>>(g, (S *)b.pop[0], b.cls, b.band_rows, (T *)b.c2, b.ptab);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (g.n_surface > 0) {
         setup_surface<T><<<(g.n_surface + 127) / 128, 128, 0, s>>>(

@@ -15,11 +15,11 @@
 //   -z             from its registers of plane p,
 //   +y, -y         from rows w-1, w+1 of plane p-1, exchanged in shared memory
 //                  (a ring of three planes: one barrier per plane).
-// The A rows that S1 of a plane pulls from (seven populations x (H+2) rows)
-// and the rows of the c^2 field are staged in shared memory by 1-D bulk (TMA)
-// copies issued two planes ahead and completing on an mbarrier (two stages);
-// the field holds, for every cell, the c^2 the update uses (c0^2, cp^2, or
-// Eq. (79) in the band), so no warp waits on a global load of its own.  No CTA waits for another
+// The A rows that S1 of a plane pulls from (seven populations x (H+2) rows),
+// their class bytes and, for rows holding interface-band cells (a per-row
+// flag from setup, read one plane ahead), their c^2 rows are staged in shared
+// memory by 1-D bulk (TMA) copies issued two planes ahead and completing on an
+// mbarrier (two stages), so no warp waits on a global load of its own.  No CTA waits for another
 // CTA: one launch reads A and writes B once, about half the HBM traffic of two
 // single steps, plus the halo rows, which neighbouring slabs read at the same
 // time (L2 hits).  Results are bit-identical to two single steps: the same
@@ -47,20 +47,11 @@ constexpr int two_step_threads() {
 }
 
 // Shared memory per S1 row: two staged planes of seven populations (storage
-// type) and of c^2 (arithmetic type), and the three-plane ring of the two
-// exchanged populations (storage type).
-constexpr size_t smem_per_row(size_t row_bytes, size_t c2_row_bytes) {
-    return (size_t)kStages * (7 * row_bytes + c2_row_bytes) + (size_t)kRingPlanes * 2 * row_bytes;
-}
-
-// W consecutive FP32 values from 16-byte aligned shared memory.
-template <int W>
-__device__ __forceinline__ void ld_f32(const float *p, float (&v)[W]) {
-#pragma unroll
-    for (int j = 0; j < W / 4; ++j) {
-        const float4 t = reinterpret_cast<const float4 *>(p)[j];
-        v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
-    }
+// type), of the class bytes and of c^2 (arithmetic type; copied only for rows
+// holding interface-band cells), and the three-plane ring of the two exchanged
+// populations (storage type).
+constexpr size_t smem_per_row(size_t row_bytes, size_t c2_row_bytes, size_t cls_row_bytes) {
+    return (size_t)kStages * (7 * row_bytes + c2_row_bytes + cls_row_bytes) + (size_t)kRingPlanes * 2 * row_bytes;
 }
 
 template <typename S> struct Vec;  // plain 16-byte shared-memory accesses
@@ -230,16 +221,19 @@ __global__ void __launch_bounds__(256) sample_two(SampleArgs<S> a, const S *__re
 
 template <typename S, int CH>
 __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
-    update2_slab(const S *__restrict__ A, S *__restrict__ B, const typename Store<S>::R *__restrict__ c2f, int nx,
-                 int ny, int nz, long long ncell, int H, int nslab, int zc, int *err) {
+    update2_slab(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ cls,
+                 const uint8_t *__restrict__ band_rows, const typename Store<S>::R *__restrict__ c2f, int nx, int ny,
+                 int nz, long long ncell, typename Store<S>::R c0sq, typename Store<S>::R cpsq, int H, int nslab,
+                 int zc, int *err) {
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
     extern __shared__ __align__(128) unsigned char smem[];
     const int rmax = H + 2;
     const size_t rowel = (size_t)nx;
-    S *stage = reinterpret_cast<S *>(smem);                                // [kStages][7][rmax][nx]
-    R *c2s = reinterpret_cast<R *>(stage + (size_t)kStages * 7 * rmax * rowel);  // [kStages][rmax][nx]
-    S *ring = reinterpret_cast<S *>(c2s + (size_t)kStages * rmax * rowel);     // [kRingPlanes][2][rmax][nx]
+    S *stage = reinterpret_cast<S *>(smem);                                          // [kStages][7][rmax][nx]
+    R *c2s = reinterpret_cast<R *>(stage + (size_t)kStages * 7 * rmax * rowel);      // [kStages][rmax][nx]
+    uint8_t *clss = reinterpret_cast<uint8_t *>(c2s + (size_t)kStages * rmax * rowel);  // [kStages][rmax][nx]
+    S *ring = reinterpret_cast<S *>(clss + (size_t)kStages * rmax * rowel);         // [kRingPlanes][2][rmax][nx]
     uint64_t *bar = reinterpret_cast<uint64_t *>(ring + (size_t)kRingPlanes * 2 * rmax * rowel);
 
     const int slab = blockIdx.x % nslab, chunk = blockIdx.x / nslab;
@@ -258,14 +252,24 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     }
     __syncthreads();
 
+    // Band flag of S1 row `lane` of plane index k (warp 0): whether its c^2
+    // row must be staged.  Loaded one plane before it is needed.
+    auto band_flag = [&](int k) -> int {
+        if (lane >= rs) return 0;
+        const int p = (za - 1 + k + nz) % nz;
+        return band_rows[(long long)p * ny + (y0 - 1 + lane + ny) % ny];
+    };
     // Stage the rows of S1 plane index k (plane za-1+k) into stage k % 2:
-    // lane i < 8 of warp 0 copies population i (i = 7: c^2) for the rs rows,
-    // one bulk copy per run of rows that is contiguous in memory (two where
-    // the slab's halo wraps around y).
-    auto issue = [&](int k) {
+    // lane i < 8 of warp 0 copies population i (i = 7: the class bytes) for
+    // the rs rows, one bulk copy per run of rows that is contiguous in memory
+    // (two where the slab's halo wraps around y); lane 8 + r copies the c^2 row
+    // of S1 row r when that row holds band cells (flag).
+    auto issue = [&](int k, int flag) {
+        const unsigned band = __ballot_sync(kFull, flag != 0);
         const int p = (za - 1 + k + nz) % nz;
         const int buf = k % kStages;
-        if (lane == 0) bar_expect(&bar[buf], (uint32_t)rs * (7u * row_bytes + c2_bytes));
+        if (lane == 0)
+            bar_expect(&bar[buf], (uint32_t)rs * (7u * row_bytes + (uint32_t)nx) + (uint32_t)__popc(band) * c2_bytes);
         __syncwarp();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage
         if (lane < 8) {
@@ -278,18 +282,24 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
                 const int len = min(rs - r, ny - yr);
                 const long long row0 = (long long)pp * ny + yr;
                 if (i == 7)
-                    bulk_load(c2s + ((size_t)buf * rmax + r) * rowel, c2f + row0 * nx, (uint32_t)len * c2_bytes,
-                              &bar[buf]);
+                    bulk_load(clss + ((size_t)buf * rmax + r) * rowel, cls + row0 * nx, (uint32_t)len * nx, &bar[buf]);
                 else
                     bulk_load(stage + ((size_t)(buf * 7 + i) * rmax + r) * rowel, A + (long long)i * ncell + row0 * nx,
                               (uint32_t)len * row_bytes, &bar[buf]);
                 r += len;
             }
+        } else if (lane - 8 < rs && ((band >> (lane - 8)) & 1u)) {
+            const int r = lane - 8;
+            const long long row0 = (long long)p * ny + (y0 - 1 + r + ny) % ny;
+            bulk_load(c2s + ((size_t)buf * rmax + r) * rowel, c2f + row0 * nx, c2_bytes, &bar[buf]);
         }
     };
+    int flag_next = 0;  // warp 0: band flag of plane index k + 2, for the issue in iteration k
     if (warp == 0) {
-        issue(0);
-        issue(1);
+        const int f0 = band_flag(0), f1 = band_flag(1);
+        flag_next = band_flag(2);
+        issue(0, f0);
+        issue(1, f1);
     }
 
     const bool s1_row = warp < rs;
@@ -310,13 +320,19 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
         if (s1_row) {
             const S *st = stage + ((size_t)buf * 7 * rmax + warp) * rowel;
             const R *cst = c2s + ((size_t)buf * rmax + warp) * rowel;
+            const uint8_t *clt = clss + ((size_t)buf * rmax + warp) * rowel;
             R f[7][CH][W];
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const int x0 = (c * 32 + lane) * W;
 #pragma unroll
                 for (int i = 0; i < 7; ++i) Vec<S>::ld(st + (size_t)i * rmax * rowel + x0, f[i][c]);
-                ld_f32<W>(cst + x0, cs[c]);
+                const unsigned long long cl = load_classes<W>(clt + x0);
+#pragma unroll
+                for (int e = 0; e < W; ++e) {  // the c^2 the one-step kernels use for the class
+                    const unsigned kc = (unsigned)(cl >> (8 * e)) & 0xffu;
+                    cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : cst[x0 + e]);
+                }
             }
             R fpx[CH][W], fmx[CH][W];
             shift_x<R, CH, W>(f[1], f[2], lane, fpx, fmx);
@@ -347,7 +363,10 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
             failed = 1;
             break;
         }
-        if (warp == 0 && k + 2 < L) issue(k + 2);
+        if (warp == 0 && k + 2 < L) {
+            issue(k + 2, flag_next);
+            flag_next = band_flag(k + 3);  // used in the next iteration
+        }
         if (k >= 2 && s2_row) {
             const int q = (p + nz - 1) % nz;
             const long long r0 = ((long long)q * ny + y) * nx;
@@ -416,7 +435,8 @@ cudaError_t plan_ch(const Geometry &g, int want, TwoStepPlan *pl) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const int ny = g.n[1], nz = g.n[2];
-    const size_t per_row = smem_per_row((size_t)g.n[0] * sizeof(S), (size_t)g.n[0] * sizeof(typename Store<S>::R));
+    const size_t per_row =
+        smem_per_row((size_t)g.n[0] * sizeof(S), (size_t)g.n[0] * sizeof(typename Store<S>::R), (size_t)g.n[0]);
     const size_t fixed = kStages * sizeof(uint64_t) + 16;
     int rows = (int)(((size_t)smem_max - fixed) / per_row);
     rows = std::min(rows, two_step_threads<S, CH>() / 32);
@@ -474,8 +494,8 @@ cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl
                                                        (const R *)b.c2);
     }
     update2_slab<S, CH><<<pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(
-        (const S *)b.pop[src], (S *)b.pop[src ^ 1], (const R *)b.c2, g.n[0], g.n[1], g.n[2], g.ncell, pl.H,
-        pl.nslab, pl.zc, err);
+        (const S *)b.pop[src], (S *)b.pop[src ^ 1], b.cls, b.band_rows, (const R *)b.c2, g.n[0], g.n[1], g.n[2],
+        g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp), pl.H, pl.nslab, pl.zc, err);
     return cudaGetLastError();
 }
 
