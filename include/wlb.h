@@ -137,6 +137,7 @@ typedef struct {
                                    wlb_set_two_step (the default where it
                                    applies)                                     */
     int two_step_rows;          /* slab height of the two-step kernel, 0 off    */
+    int two_step_segments;      /* warps per lattice row in it, 0 off           */
 } wlb_info;
 
 /* Check a parameter set.  WLB_ERR_ARG for: unknown lattice or precision,
@@ -347,9 +348,12 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
  * of both steps (t from the stored state, t+1 recomputed from it by the same
  * arithmetic), in the order two single steps add them.  On by default (set
  * up by wlb_create with an automatic slab height) wherever it is supported:
- * 3D, periodic boundaries, FP32 rows of nx = 128 or 256 cells or FP16 rows of
- * nx = 256 (one warp per row).  Elsewhere, or with enable = 0, every step is
- * one launch.  enable: 0 off, nonzero on (WLB_ERR_ARG if unsupported).
+ * 3D, periodic boundaries, FP32 or FP16 storage, nx a multiple of 128 (FP32)
+ * or 256 (FP16) cells, each row split into warp-wide segments, and at least
+ * one slab row fitting the shared memory (nx up to about 1500 FP32 cells).
+ * Elsewhere, or with enable = 0, every step is one launch.  enable: 0 off;
+ * 1 on, lane layout chosen by the library; 2 on with one 16-byte chunk per
+ * lane (more, lighter warps); 3 on with two (WLB_ERR_ARG if unsupported).
  * slab_rows: 0 lets the library choose (largest slab the shared memory
  * holds, z chunked to fill the SMs), else that height (WLB_ERR_ARG if it does
  * not fit; the setting is then unchanged).  A stalled staging copy (bounded

@@ -56,6 +56,7 @@ class Info(ctypes.Structure):
         ("bytes_per_update", ctypes.c_double), ("vector_path", ctypes.c_int),
         ("steps_per_launch", ctypes.c_int),
         ("two_step_rows", ctypes.c_int),
+        ("two_step_segments", ctypes.c_int),
     ]
 
 
@@ -231,9 +232,11 @@ class Solver:
     def init(self):
         _check(lib().wlb_init(self._h), self._h, "wlb_init")
 
-    def set_two_step(self, enable=True, slab_rows=0):
-        """Unsampled steps two per launch (wlb_set_two_step)."""
-        _check(lib().wlb_set_two_step(self._h, 1 if enable else 0, int(slab_rows)), self._h, "wlb_set_two_step")
+    def set_two_step(self, enable=True, slab_rows=0, chunks_per_lane=0):
+        """Steps two per launch (wlb_set_two_step); chunks_per_lane 0 lets the
+        library choose, 1 or 2 asks for that lane layout."""
+        mode = (1 + int(chunks_per_lane)) if enable else 0
+        _check(lib().wlb_set_two_step(self._h, mode, int(slab_rows)), self._h, "wlb_set_two_step")
 
     def step(self, n, sample=False):
         _check(lib().wlb_step(self._h, int(n), 1 if sample else 0), self._h, "wlb_step")

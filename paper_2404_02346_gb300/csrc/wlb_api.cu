@@ -146,7 +146,7 @@ cudaError_t issue_period(wlb_handle *h, int start, bool sampled, cudaStream_t s)
     long long t = 0;
     if (h->two_step)
         for (; t + 1 < h->period; t += 2) {  // two steps per launch
-            cudaError_t e = wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, cur, sampled, h->b.err, s);
+            cudaError_t e = wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, cur, sampled, h->b.err, s, h->side);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -285,13 +285,16 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
     }
     layout(h->g, h->prec, base, &h->b);
     e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->host_out, 8 * sizeof(double), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         wlb_destroy(h);
         return WLB_ERR_CUDA;
     }
     // unsampled steps two per launch wherever the kernel applies (bit-identical)
-    if (wlb::two_step_supported(h->g, h->prec) && wlb::plan_two_steps(h->g, h->prec, 0, &h->two_plan) == cudaSuccess)
+    if (wlb::two_step_supported(h->g, h->prec) && wlb::plan_two_steps(h->g, h->prec, 0, 1, &h->two_plan) == cudaSuccess)
         h->two_step = true;
     cudaGetLastError();
     *out = h;
@@ -327,7 +330,8 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
             continue;
         }
         if (h->two_step && n >= 2 && (!sampled || h->samples_in_period + 2 <= h->period)) {
-            WLB_CUDA(h, wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, h->src, sampled, h->b.err, h->stream),
+            WLB_CUDA(h, wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, h->src, sampled, h->b.err, h->stream,
+                                              h->side),
                      "two-step kernels");
             h->src ^= 1;
             h->steps_done += 2;
@@ -438,16 +442,17 @@ wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out) {
 }
 
 wlb_status wlb_set_two_step(wlb_handle *h, int enable, int slab_rows) {
-    if (!h || slab_rows < 0) return WLB_ERR_ARG;
-    if (enable && !wlb::two_step_supported(h->g, h->prec))
-        return fail(h, WLB_ERR_ARG, "two steps per launch need a 3D periodic FP32/FP16 lattice of one-warp rows");
+    if (!h || slab_rows < 0 || enable < 0 || enable > 3) return WLB_ERR_ARG;
     DeviceGuard dg(h->device);
+    if (enable && !wlb::two_step_supported(h->g, h->prec))
+        return fail(h, WLB_ERR_ARG, "two steps per launch need a 3D periodic FP32/FP16 lattice of warp-wide rows");
     wlb::TwoStepPlan plan;
     if (enable) {
-        cudaError_t e = wlb::plan_two_steps(h->g, h->prec, slab_rows, &plan);
-        if (e != cudaSuccess) return fail(h, WLB_ERR_ARG, "slab height does not fit the shared memory", e);
+        cudaError_t e = wlb::plan_two_steps(h->g, h->prec, slab_rows, enable, &plan);
+        if (e != cudaSuccess) return fail(h, WLB_ERR_ARG, "slab height or lane layout does not fit", e);
     }
-    const bool same = (enable != 0) == h->two_step && plan.H == h->two_plan.H && plan.zc == h->two_plan.zc;
+    const bool same = (enable != 0) == h->two_step && plan.H == h->two_plan.H && plan.zc == h->two_plan.zc &&
+                      plan.nseg == h->two_plan.nseg && plan.chunks_per_lane == h->two_plan.chunks_per_lane;
     if (!same) {
         destroy_graphs(h);  // unsampled period graphs change shape
         h->two_step = enable != 0;
@@ -470,6 +475,7 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out) {
     out->vector_path = h->vector_path ? 1 : 0;
     out->steps_per_launch = h->two_step ? 2 : 1;
     out->two_step_rows = h->two_step ? h->two_plan.H : 0;
+    out->two_step_segments = h->two_step ? h->two_plan.nseg : 0;
     return WLB_OK;
 }
 
@@ -478,6 +484,9 @@ wlb_status wlb_destroy(wlb_handle *h) {
     DeviceGuard dg(h->device);
     destroy_graphs(h);
     if (h->capture) cudaStreamDestroy(h->capture);
+    if (h->side.stream) cudaStreamDestroy(h->side.stream);
+    if (h->side.fork) cudaEventDestroy(h->side.fork);
+    if (h->side.join) cudaEventDestroy(h->side.join);
     if (h->host_out) cudaFreeHost(h->host_out);
     if (h->owned) cudaFree(h->owned);
     delete h;

@@ -29,6 +29,7 @@ struct wlb_handle {
     bool vector_path = false;
     bool two_step = false;      // unsampled steps two per launch (wlb_set_two_step)
     wlb::TwoStepPlan two_plan;  // its grid, set by wlb_set_two_step
+    wlb::SideStream side;       // sampling beside the two-step update
     char err[512] = {0};
 };
 

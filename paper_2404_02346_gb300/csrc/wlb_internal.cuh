@@ -71,20 +71,30 @@ cudaError_t launch_fields(const Geometry &g, const Buffers &b, Prec p, int src,
                           long long first_cell, long long count, cudaStream_t s);
 bool update_is_vectorised(const Geometry &g, Prec p);
 
-// Two steps per launch (wlb_two_step.cu): 3D, periodic, FP32 or
-// FP16 rows of one warp (up to 8 values per lane).  Slab height H, slabs and
-// z-chunks of the grid, block size and dynamic shared memory.
+// Two steps per launch (wlb_two_step.cu): 3D, periodic, FP32 or FP16 rows
+// that are whole numbers of warp-wide 16-byte vectors, split into nseg
+// segments of one warp each.  Slab height H, slabs and z-chunks of the grid,
+// segments per row, chunks per lane, block size and dynamic shared memory.
 struct TwoStepPlan {
-    int H = 0, nslab = 0, chunks = 0, zc = 0, threads = 0;
+    int H = 0, nslab = 0, chunks = 0, zc = 0, nseg = 0, chunks_per_lane = 0, threads = 0;
     size_t smem = 0;
 };
 bool two_step_supported(const Geometry &g, Prec p);
-// slab_rows: 0 picks H; otherwise that H.  Also opts the kernel into the
-// shared memory it needs on the current device.
-cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, TwoStepPlan *out);
+// slab_rows: 0 picks H; otherwise that H.  mode: 1 automatic, 2 one 16-byte
+// chunk per lane, 3 two.  Also opts the kernel into the shared memory it needs
+// on the current device.
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, TwoStepPlan *out);
+// Side stream and events that let the sampling kernel of a sampled two-step
+// launch run beside the update (fork before, join after).
+struct SideStream {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
 // From buffer src into src ^ 1; with sample, the surface sums of both steps
-// are accumulated too (a sampling kernel before the update).
+// are accumulated too by a sampling kernel that reads only src, forked onto
+// side.stream and joined back into s after the update is enqueued (on s
+// itself when side.stream is null).
 cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src, bool sample,
-                             int *err, cudaStream_t s);
+                             int *err, cudaStream_t s, const SideStream &side);
 
 }  // namespace wlb

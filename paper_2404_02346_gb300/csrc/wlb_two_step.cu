@@ -65,6 +65,11 @@ template <> struct Vec<float> {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
     __device__ static float rounded(float v) { return v; }
+    __device__ static void rounded(const float (&in)[4], float (&out)[4]) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) out[e] = in[e];
+    }
+    __device__ static float get(const float *p) { return *p; }
 };
 
 template <> struct Vec<__half> {
@@ -91,6 +96,15 @@ template <> struct Vec<__half> {
     }
     // the value a single step would store and the next step read back
     __device__ static float rounded(float v) { return __half2float(__float2half_rn(v)); }
+    __device__ static void rounded(const float (&in)[8], float (&out)[8]) {  // pairwise, same rounding
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const float2 f = __half22float2(__floats2half2_rn(in[e], in[e + 1]));
+            out[e] = f.x;
+            out[e + 1] = f.y;
+        }
+    }
+    __device__ static float get(const __half *p) { return __half2float(*p); }
 };
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -138,11 +152,16 @@ __device__ __forceinline__ void collide7(R c2, R f0, R fpx, R fmx, R fpy, R fmy,
     collide_half<R, 3>(c2, f, o);
 }
 
-// +x / -x pulls of a warp-wide row held as CH chunks of W values per lane
-// (x = (c * 32 + lane) * W + e): value from x - 1 and from x + 1, periodic.
+// +x / -x pulls of a warp's segment of a row, held as CH chunks of W values
+// per lane (x = xs + (c * 32 + lane) * W + e): the value from x - 1 and from
+// x + 1.  Inside the segment they come by shuffles; at its ends from `left`
+// (the +x value at xs - 1, used by lane 0) and `right` (the -x value at the
+// first cell past the segment, used by lane 31), both periodic in x.  With
+// `whole` (the segment is the whole row) the ends wrap around by shuffles and
+// left / right are not read.
 template <typename R, int CH, int W>
-__device__ __forceinline__ void shift_x(const R (&px)[CH][W], const R (&mx)[CH][W], int lane, R (&fpx)[CH][W],
-                                        R (&fmx)[CH][W]) {
+__device__ __forceinline__ void shift_x(const R (&px)[CH][W], const R (&mx)[CH][W], int lane, bool whole, R left,
+                                        R right, R (&fpx)[CH][W], R (&fmx)[CH][W]) {
     R up[CH], dn[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -151,12 +170,12 @@ __device__ __forceinline__ void shift_x(const R (&px)[CH][W], const R (&mx)[CH][
     }
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
-        fpx[c][0] = lane == 0 ? up[(c + CH - 1) % CH] : up[c];
+        fpx[c][0] = lane == 0 ? (c == 0 ? (whole ? up[CH - 1] : left) : up[c - 1]) : up[c];
 #pragma unroll
         for (int e = 1; e < W; ++e) fpx[c][e] = px[c][e - 1];
 #pragma unroll
         for (int e = 0; e < W - 1; ++e) fmx[c][e] = mx[c][e + 1];
-        fmx[c][W - 1] = lane == 31 ? dn[(c + 1) % CH] : dn[c];
+        fmx[c][W - 1] = lane == 31 ? (c == CH - 1 ? (whole ? dn[0] : right) : dn[c + 1]) : dn[c];
     }
 }
 
@@ -224,7 +243,7 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     update2_slab(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ cls,
                  const uint8_t *__restrict__ band_rows, const typename Store<S>::R *__restrict__ c2f, int nx, int ny,
                  int nz, long long ncell, typename Store<S>::R c0sq, typename Store<S>::R cpsq, int H, int nslab,
-                 int zc, int *err) {
+                 int zc, int nseg, int *err) {
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -234,7 +253,9 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     R *c2s = reinterpret_cast<R *>(stage + (size_t)kStages * 7 * rmax * rowel);      // [kStages][rmax][nx]
     uint8_t *clss = reinterpret_cast<uint8_t *>(c2s + (size_t)kStages * rmax * rowel);  // [kStages][rmax][nx]
     S *ring = reinterpret_cast<S *>(clss + (size_t)kStages * rmax * rowel);         // [kRingPlanes][2][rmax][nx]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(ring + (size_t)kRingPlanes * 2 * rmax * rowel);
+    R *edge = reinterpret_cast<R *>(ring + (size_t)kRingPlanes * 2 * rmax * rowel);  // [kRingPlanes][rmax][nseg][2]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(edge + (size_t)kRingPlanes * rmax * nseg * 2);  // [kStages]
+    uint8_t *rowflag = reinterpret_cast<uint8_t *>(bar + kStages);  // [kStages][rmax]: row holds band cells
 
     const int slab = blockIdx.x % nslab, chunk = blockIdx.x / nslab;
     const int y0 = slab * H;
@@ -268,6 +289,7 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
         const unsigned band = __ballot_sync(kFull, flag != 0);
         const int p = (za - 1 + k + nz) % nz;
         const int buf = k % kStages;
+        if (lane < rs) rowflag[buf * rmax + lane] = flag != 0;  // read by S1 after a barrier
         if (lane == 0)
             bar_expect(&bar[buf], (uint32_t)rs * (7u * row_bytes + (uint32_t)nx) + (uint32_t)__popc(band) * c2_bytes);
         __syncwarp();
@@ -301,10 +323,16 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
         issue(0, f0);
         issue(1, f1);
     }
+    __syncthreads();  // row flags of stages 0 and 1
 
-    const bool s1_row = warp < rs;
-    const bool s2_row = warp >= 1 && warp <= hs;
-    const int y = (y0 - 1 + warp + ny) % ny;
+    // warp -> S1 row `row` of the slab (y0-1+row) and segment `seg` of it
+    // (cells xs .. xs + 32*W*CH - 1)
+    const int row = warp / nseg, seg = warp % nseg;
+    const int xs = seg * 32 * W * CH;
+    const bool whole = nseg == 1;  // one warp per row: x wraps by shuffles
+    const bool s1_row = row < rs;
+    const bool s2_row = row >= 1 && row <= hs;
+    const int y = (y0 - 1 + row + ny) % ny;
     // registers carried between planes (S1 results in storage precision)
     R n0[CH][W], n1[CH][W], n2[CH][W];  // rest, +x, -x of plane p-1
     R pz0[CH][W], pz1[CH][W];           // +z of planes p-2, p-1
@@ -318,44 +346,67 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
         R c0v[CH][W], c1v[CH][W], c2v[CH][W], c5v[CH][W], c6v[CH][W];
         R cs[CH][W];
         if (s1_row) {
-            const S *st = stage + ((size_t)buf * 7 * rmax + warp) * rowel;
-            const R *cst = c2s + ((size_t)buf * rmax + warp) * rowel;
-            const uint8_t *clt = clss + ((size_t)buf * rmax + warp) * rowel;
+            const S *st = stage + ((size_t)buf * 7 * rmax + row) * rowel;
+            const R *cst = c2s + ((size_t)buf * rmax + row) * rowel;
+            const uint8_t *clt = clss + ((size_t)buf * rmax + row) * rowel;
+            const bool band_row = rowflag[buf * rmax + row] != 0;  // warp-uniform
             R f[7][CH][W];
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const int x0 = (c * 32 + lane) * W;
+                const int x0 = xs + (c * 32 + lane) * W;
 #pragma unroll
                 for (int i = 0; i < 7; ++i) Vec<S>::ld(st + (size_t)i * rmax * rowel + x0, f[i][c]);
+                // the c^2 the one-step kernels use for the class; a row without
+                // interface-band cells holds only fluid and object cells
                 const unsigned long long cl = load_classes<W>(clt + x0);
+                if (band_row) {
 #pragma unroll
-                for (int e = 0; e < W; ++e) {  // the c^2 the one-step kernels use for the class
-                    const unsigned kc = (unsigned)(cl >> (8 * e)) & 0xffu;
-                    cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : cst[x0 + e]);
+                    for (int e = 0; e < W; ++e) {
+                        const unsigned kc = (unsigned)(cl >> (8 * e)) & 0xffu;
+                        cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : cst[x0 + e]);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < W; ++e)
+                        cs[c][e] = ((unsigned)(cl >> (8 * e)) & 0xffu) == CELL_FLUID ? c0sq : cpsq;
                 }
             }
+            // ends of the segment from the staged row (periodic in x)
+            R left = R(0), right = R(0);
+            if (!whole) {
+                left = Vec<S>::get(st + (size_t)1 * rmax * rowel + (xs + nx - 1) % nx);
+                right = Vec<S>::get(st + (size_t)2 * rmax * rowel + (xs + 32 * W * CH) % nx);
+            }
             R fpx[CH][W], fmx[CH][W];
-            shift_x<R, CH, W>(f[1], f[2], lane, fpx, fmx);
-            S *ry = ring + ((size_t)(k % kRingPlanes) * 2 * rmax + warp) * rowel;
+            shift_x<R, CH, W>(f[1], f[2], lane, whole, left, right, fpx, fmx);
+            S *ry = ring + ((size_t)(k % kRingPlanes) * 2 * rmax + row) * rowel;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const int x0 = (c * 32 + lane) * W;
-                R oy[W], omy[W];
+                const int x0 = xs + (c * 32 + lane) * W;
+                R o[7][W];
 #pragma unroll
                 for (int e = 0; e < W; ++e) {
-                    R o[7];
+                    R t[7];
                     collide7(cs[c][e], f[0][c][e], fpx[c][e], fmx[c][e], f[3][c][e], f[4][c][e], f[5][c][e],
-                             f[6][c][e], o);
-                    c0v[c][e] = Vec<S>::rounded(o[0]);
-                    c1v[c][e] = Vec<S>::rounded(o[1]);
-                    c2v[c][e] = Vec<S>::rounded(o[2]);
-                    oy[e] = o[3];
-                    omy[e] = o[4];
-                    c5v[c][e] = Vec<S>::rounded(o[5]);
-                    c6v[c][e] = Vec<S>::rounded(o[6]);
+                             f[6][c][e], t);
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) o[i][e] = t[i];
                 }
+                Vec<S>::rounded(o[0], c0v[c]);
+                Vec<S>::rounded(o[1], c1v[c]);
+                Vec<S>::rounded(o[2], c2v[c]);
+                Vec<S>::rounded(o[5], c5v[c]);
+                Vec<S>::rounded(o[6], c6v[c]);
+                const R (&oy)[W] = o[3];
+                const R (&omy)[W] = o[4];
                 Vec<S>::st(ry + x0, oy);                        // +y of row w
                 Vec<S>::st(ry + (size_t)rmax * rowel + x0, omy);  // -y of row w
+            }
+            // the segment's end values for the neighbouring segments' S2
+            if (!whole) {
+                R *ed = edge + ((size_t)(k % kRingPlanes) * rmax + row) * nseg * 2 + seg * 2;
+                if (lane == 31) ed[0] = c1v[CH - 1][W - 1];  // +x at the last cell
+                if (lane == 0) ed[1] = c2v[0][0];            // -x at the first cell
             }
         }
         // stage `buf` consumed, ring plane k written; any failed wait ends the sweep
@@ -371,14 +422,20 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
             const int q = (p + nz - 1) % nz;
             const long long r0 = ((long long)q * ny + y) * nx;
             const S *ry = ring + (size_t)((k - 1) % kRingPlanes) * 2 * rmax * rowel;
+            R left = R(0), right = R(0);
+            if (!whole) {
+                const R *ed = edge + ((size_t)((k - 1) % kRingPlanes) * rmax + row) * nseg * 2;
+                left = ed[((seg + nseg - 1) % nseg) * 2];  // +x at the previous segment's last cell
+                right = ed[((seg + 1) % nseg) * 2 + 1];    // -x at the next segment's first cell
+            }
             R fpx[CH][W], fmx[CH][W];
-            shift_x<R, CH, W>(n1, n2, lane, fpx, fmx);
+            shift_x<R, CH, W>(n1, n2, lane, whole, left, right, fpx, fmx);
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const int x0 = (c * 32 + lane) * W;
+                const int x0 = xs + (c * 32 + lane) * W;
                 R fpy[W], fmy[W];
-                Vec<S>::ld(ry + (size_t)(warp - 1) * rowel + x0, fpy);             // +y of row w-1
-                Vec<S>::ld(ry + (size_t)(rmax + warp + 1) * rowel + x0, fmy);      // -y of row w+1
+                Vec<S>::ld(ry + (size_t)(row - 1) * rowel + x0, fpy);             // +y of row w-1
+                Vec<S>::ld(ry + (size_t)(rmax + row + 1) * rowel + x0, fmy);      // -y of row w+1
                 R o[7][W];
 #pragma unroll
                 for (int e = 0; e < W; ++e) {
@@ -413,12 +470,22 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     }
 }
 
+// 16-byte vectors per lane across a whole row, or 0 if a row is not a whole
+// number of warp-wide vectors.
 template <typename S>
-int chunks_of(const Geometry &g) {
+int row_vectors(const Geometry &g) {
     constexpr int W = Store<S>::W;
-    if (g.n[0] % (32 * W)) return 0;
-    const int ch = g.n[0] / (32 * W);
-    return (ch >= 1 && W * ch <= 8) ? ch : 0;
+    return g.n[0] % (32 * W) ? 0 : g.n[0] / (32 * W);
+}
+
+// Chunks per lane for a row of v vectors per lane: two where they divide the
+// row and fit the registers (mode 3 asks for two), one with mode 2.
+template <typename S>
+int chunks_for(int v, int mode) {
+    const bool two_fit = Store<S>::W * 2 <= 8 && v % 2 == 0;
+    if (mode == 2) return 1;
+    if (mode == 3) return two_fit ? 2 : 0;
+    return two_fit ? 2 : 1;
 }
 
 // Slab height H (rows <= smem and thread limits; `want` > 0 asks for one)
@@ -428,7 +495,7 @@ int chunks_of(const Geometry &g) {
 // costs a CTA a fixed latency besides its bytes, so fewer, taller slabs win
 // where the bytes alone do not decide.
 template <typename S, int CH>
-cudaError_t plan_ch(const Geometry &g, int want, TwoStepPlan *pl) {
+cudaError_t plan_ch(const Geometry &g, int want, int nseg, TwoStepPlan *pl) {
     int dev = 0, sms = 0, smem_max = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -437,9 +504,10 @@ cudaError_t plan_ch(const Geometry &g, int want, TwoStepPlan *pl) {
     const int ny = g.n[1], nz = g.n[2];
     const size_t per_row =
         smem_per_row((size_t)g.n[0] * sizeof(S), (size_t)g.n[0] * sizeof(typename Store<S>::R), (size_t)g.n[0]);
-    const size_t fixed = kStages * sizeof(uint64_t) + 16;
-    int rows = (int)(((size_t)smem_max - fixed) / per_row);
-    rows = std::min(rows, two_step_threads<S, CH>() / 32);
+    const size_t per_row_all = per_row + (size_t)kRingPlanes * nseg * 2 * sizeof(typename Store<S>::R);
+    const size_t fixed = kStages * sizeof(uint64_t) + kStages * (size_t)kMaxRows + 16;
+    int rows = (int)(((size_t)smem_max - fixed) / per_row_all);
+    rows = std::min(rows, two_step_threads<S, CH>() / (32 * nseg));
     if (rows < 3) return cudaErrorInvalidValue;
     const int h_lo = want > 0 ? want : 1, h_hi = want > 0 ? want : rows - 2;
     if (h_hi > rows - 2) return cudaErrorInvalidValue;
@@ -468,75 +536,91 @@ cudaError_t plan_ch(const Geometry &g, int want, TwoStepPlan *pl) {
             *pl = per_h[H];
             break;
         }
-    pl->threads = 32 * (pl->H + 2);
-    pl->smem = per_row * (pl->H + 2) + fixed;
+    pl->nseg = nseg;
+    pl->chunks_per_lane = CH;
+    pl->threads = 32 * nseg * (pl->H + 2);
+    pl->smem = per_row_all * (pl->H + 2) + fixed;
     return cudaFuncSetAttribute(update2_slab<S, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
 }
 
+// Chunks per lane and segments per row for `mode` (1: automatic, 2: one
+// chunk, 3: two), then the slab plan.
 template <typename S>
-cudaError_t plan_for(const Geometry &g, int want, TwoStepPlan *pl) {
-    switch (chunks_of<S>(g)) {
-        case 1: return plan_ch<S, 1>(g, want, pl);
-        case 2:
-            if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, pl);
-            return cudaErrorInvalidValue;
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t plan_for(const Geometry &g, int want, int mode, TwoStepPlan *pl) {
+    const int v = row_vectors<S>(g);
+    const int ch = v ? chunks_for<S>(v, mode) : 0;
+    if (!ch) return cudaErrorInvalidValue;
+    if (ch == 1) return plan_ch<S, 1>(g, want, v, pl);
+    if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, v / 2, pl);
+    return cudaErrorInvalidValue;
 }
 
+// The sampling kernel runs in 128-thread blocks so that one fits on an SM
+// beside a two-step CTA (registers), and on the SMs the grid leaves free.
 template <typename S, int CH>
 cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, bool sample, int *err,
-                      cudaStream_t s) {
+                      cudaStream_t s, const SideStream &side) {
     using R = typename Store<S>::R;
+    const bool fork = sample && g.n_surface > 0 && side.stream;
+    cudaError_t e = cudaSuccess;
+    if (fork) {
+        e = cudaEventRecord(side.fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side.stream, side.fork, 0);
+        if (e != cudaSuccess) return e;
+    }
     if (sample && g.n_surface > 0) {
-        const long long blocks = ((long long)g.n_surface * 32 + 255) / 256;
-        sample_two<S><<<(unsigned)blocks, 256, 0, s>>>(sample_args<S>(g, b), (const S *)b.pop[src],
-                                                       (const R *)b.c2);
+        const long long blocks = ((long long)g.n_surface * 32 + 127) / 128;
+        sample_two<S><<<(unsigned)blocks, 128, 0, fork ? side.stream : s>>>(sample_args<S>(g, b),
+                                                                            (const S *)b.pop[src], (const R *)b.c2);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && fork) e = cudaEventRecord(side.join, side.stream);
+        if (e != cudaSuccess) return e;
     }
     update2_slab<S, CH><<<pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(
         (const S *)b.pop[src], (S *)b.pop[src ^ 1], b.cls, b.band_rows, (const R *)b.c2, g.n[0], g.n[1], g.n[2],
-        g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp), pl.H, pl.nslab, pl.zc, err);
-    return cudaGetLastError();
+        g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp), pl.H, pl.nslab, pl.zc, pl.nseg, err);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(s, side.join, 0);  // the next launch overwrites src
+    return e;
 }
 
 template <typename S>
 cudaError_t launch_for(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, bool sample, int *err,
-                       cudaStream_t s) {
-    switch (chunks_of<S>(g)) {
-        case 1: return launch_ch<S, 1>(g, b, pl, src, sample, err, s);
-        case 2:
-            if constexpr (Store<S>::W * 2 <= 8) return launch_ch<S, 2>(g, b, pl, src, sample, err, s);
-            return cudaErrorInvalidValue;
-        default: return cudaErrorInvalidValue;
-    }
+                       cudaStream_t s, const SideStream &side) {
+    if (pl.chunks_per_lane == 1) return launch_ch<S, 1>(g, b, pl, src, sample, err, s, side);
+    if constexpr (Store<S>::W * 2 <= 8)
+        if (pl.chunks_per_lane == 2) return launch_ch<S, 2>(g, b, pl, src, sample, err, s, side);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 bool two_step_supported(const Geometry &g, Prec p) {
     if (g.dim != 3 || g.driven) return false;
+    TwoStepPlan probe;
     switch (p) {
-        case Prec::F16: return chunks_of<__half>(g) > 0;
-        case Prec::F32: return chunks_of<float>(g) > 0;
+        case Prec::F16: return row_vectors<__half>(g) > 0 && plan_for<__half>(g, 0, 1, &probe) == cudaSuccess;
+        case Prec::F32: return row_vectors<float>(g) > 0 && plan_for<float>(g, 0, 1, &probe) == cudaSuccess;
         default: return false;
     }
 }
 
-cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, TwoStepPlan *out) {
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, TwoStepPlan *out) {
     TwoStepPlan pl;
-    if (!two_step_supported(g, p)) return cudaErrorInvalidValue;
-    cudaError_t e = p == Prec::F16 ? plan_for<__half>(g, slab_rows, &pl) : plan_for<float>(g, slab_rows, &pl);
+    if (g.dim != 3 || g.driven || (p != Prec::F16 && p != Prec::F32)) return cudaErrorInvalidValue;
+    cudaError_t e = p == Prec::F16 ? plan_for<__half>(g, slab_rows, mode, &pl)
+                                   : plan_for<float>(g, slab_rows, mode, &pl);
     if (e == cudaSuccess) *out = pl;
     return e;
 }
 
 // Two steps from buffer src into src ^ 1, sampling both when asked.
 cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src, bool sample,
-                             int *err, cudaStream_t s) {
+                             int *err, cudaStream_t s, const SideStream &side) {
     if (!pl.H) return cudaErrorInvalidValue;
     switch (p) {
-        case Prec::F16: return launch_for<__half>(g, b, pl, src, sample, err, s);
-        case Prec::F32: return launch_for<float>(g, b, pl, src, sample, err, s);
+        case Prec::F16: return launch_for<__half>(g, b, pl, src, sample, err, s, side);
+        case Prec::F32: return launch_for<float>(g, b, pl, src, sample, err, s, side);
         default: return cudaErrorInvalidValue;
     }
 }

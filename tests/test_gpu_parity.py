@@ -308,18 +308,20 @@ def test_driven_cavity_steps_split_across_calls(wlb):
 
 # --- two unsampled steps per launch (slab temporal blocking) --------------------------
 
-def _two_step_outputs(wlb, prob, precision, settings, tail_steps=3):
+def _two_step_outputs(wlb, prob, precision, settings, tail_steps=3, chunks_per_lane=0, segments=None):
     """Force of the whole protocol, then `tail_steps` more unsampled steps
     (direct launches: one two-step launch and one single step for 3) and the
     fields, for each (enable, slab_rows) in settings."""
     out = []
     for enable, rows in settings:
         with wlb.Solver(prob, precision=precision) as s:
-            s.set_two_step(bool(enable), rows)
+            s.set_two_step(bool(enable), rows, chunks_per_lane)
             if enable:
                 info = s.info()
                 assert info.steps_per_launch == 2
                 assert info.two_step_rows == (rows or info.two_step_rows) and info.two_step_rows > 0
+                if segments is not None:
+                    assert info.two_step_segments == segments
             F = s.run()
             s.step(tail_steps)
             p1, u1 = s.fields()
@@ -327,18 +329,25 @@ def _two_step_outputs(wlb, prob, precision, settings, tail_steps=3):
     return out
 
 
-@pytest.mark.parametrize("shape,lam,precision,rows", [
-    ((128, 48, 64), 32.0, "f32", (0, 1, 5, 14)),   # one chunk per lane; ragged slabs for 5 and 14
-    ((256, 24, 32), 16.0, "f32", (0, 3, 7, 8)),    # two chunks per lane
-    ((128, 37, 48), 16.0, "f32", (0, 4, 11)),      # odd ny: ragged slabs; uneven z chunks
-    ((256, 40, 32), 16.0, "f16", (0, 2, 9)),       # FP16 storage: t+1 rounded as stored
+@pytest.mark.parametrize("shape,lam,precision,rows,cpl,segments", [
+    ((128, 48, 64), 32.0, "f32", (0, 1, 5, 14), 0, 1),   # one chunk per lane; ragged slabs for 5 and 14
+    ((256, 24, 32), 16.0, "f32", (0, 3, 7, 8), 0, 1),    # two chunks per lane
+    ((256, 24, 32), 16.0, "f32", (0, 2, 6), 1, 2),       # one chunk per lane: two warps per row
+    ((128, 37, 48), 16.0, "f32", (0, 4, 11), 0, 1),      # odd ny: ragged slabs; uneven z chunks
+    ((512, 24, 32), 16.0, "f32", (0, 1, 3), 0, 2),       # two warps of two chunks per row
+    ((512, 22, 32), 16.0, "f32", (0, 2), 1, 4),          # four warps of one chunk per row
+    ((384, 21, 32), 16.0, "f32", (0, 3), 0, 3),          # three one-chunk segments per row
+    ((256, 40, 32), 16.0, "f16", (0, 2, 9), 0, 1),       # FP16 storage: t+1 rounded as stored
+    ((512, 24, 32), 16.0, "f16", (0, 3), 0, 2),          # FP16, two warps per row
 ])
-def test_two_step_is_bit_identical(wlb, shape, lam, precision, rows):
+def test_two_step_is_bit_identical(wlb, shape, lam, precision, rows, cpl, segments):
     """Same per-cell arithmetic as two single steps: forces and fields equal bit
-    for bit, for several slab heights (ragged last slabs and z chunks)."""
+    for bit, for several slab heights (ragged last slabs and z chunks) and rows
+    split over one to four warps (segment ends exchanged through shared memory)."""
     prob = workloads.problem(3, shape, 2, lam, 3.0, (shape[0] / 2 + 0.25, shape[1] / 2 - 0.5, lam / 8),
                              cp=0.42, n_surface=200, n_periods=6, n_avg_periods=2)
-    out = _two_step_outputs(wlb, prob, precision, [(0, 0)] + [(1, r) for r in rows])
+    out = _two_step_outputs(wlb, prob, precision, [(0, 0)] + [(1, r) for r in rows], chunks_per_lane=cpl,
+                            segments=segments)
     for o in out[1:]:
         assert np.array_equal(out[0][0], o[0])
         assert np.array_equal(out[0][1], o[1])
