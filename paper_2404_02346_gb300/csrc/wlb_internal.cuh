@@ -77,6 +77,7 @@ bool update_is_vectorised(const Geometry &g, Prec p);
 // segments per row, chunks per lane, block size and dynamic shared memory.
 struct TwoStepPlan {
     int H = 0, nslab = 0, chunks = 0, zc = 0, nseg = 0, chunks_per_lane = 0, threads = 0;
+    bool full = false;  // every segment a full warp (no idle lanes)
     size_t smem = 0;
 };
 bool two_step_supported(const Geometry &g, Prec p);

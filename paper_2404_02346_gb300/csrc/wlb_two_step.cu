@@ -153,15 +153,15 @@ __device__ __forceinline__ void collide7(R c2, R f0, R fpx, R fmx, R fpy, R fmy,
 }
 
 // +x / -x pulls of a warp's segment of a row, held as CH chunks of W values
-// per lane (x = xs + (c * 32 + lane) * W + e): the value from x - 1 and from
-// x + 1.  Inside the segment they come by shuffles; at its ends from `left`
-// (the +x value at xs - 1, used by lane 0) and `right` (the -x value at the
-// first cell past the segment, used by lane 31), both periodic in x.  With
-// `whole` (the segment is the whole row) the ends wrap around by shuffles and
-// left / right are not read.
+// per lane in slots j = c * 32 + lane (x = xs + j * W + e), of which the first
+// vg are cells: the value from x - 1 and from x + 1.  Inside the segment they
+// come by shuffles; at its ends from `left` (the +x value at xs - 1, used by
+// slot 0) and `right` (the -x value at the first cell past the segment, used
+// by slot vg - 1), both periodic in x.  With `whole` (one full segment is the
+// whole row) the ends wrap around by shuffles and left / right are not read.
 template <typename R, int CH, int W>
-__device__ __forceinline__ void shift_x(const R (&px)[CH][W], const R (&mx)[CH][W], int lane, bool whole, R left,
-                                        R right, R (&fpx)[CH][W], R (&fmx)[CH][W]) {
+__device__ __forceinline__ void shift_x(const R (&px)[CH][W], const R (&mx)[CH][W], int lane, int vg, bool whole,
+                                        R left, R right, R (&fpx)[CH][W], R (&fmx)[CH][W]) {
     R up[CH], dn[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -175,7 +175,8 @@ __device__ __forceinline__ void shift_x(const R (&px)[CH][W], const R (&mx)[CH][
         for (int e = 1; e < W; ++e) fpx[c][e] = px[c][e - 1];
 #pragma unroll
         for (int e = 0; e < W - 1; ++e) fmx[c][e] = mx[c][e + 1];
-        fmx[c][W - 1] = lane == 31 ? (c == CH - 1 ? (whole ? dn[0] : right) : dn[c + 1]) : dn[c];
+        const R next = lane == 31 ? (c == CH - 1 ? (whole ? dn[0] : right) : dn[c + 1]) : dn[c];
+        fmx[c][W - 1] = (!whole && c * 32 + lane == vg - 1) ? right : next;
     }
 }
 
@@ -238,12 +239,14 @@ __global__ void __launch_bounds__(256) sample_two(SampleArgs<S> a, const S *__re
     });
 }
 
-template <typename S, int CH>
+template <typename S, int CH, bool FULL>
 __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     update2_slab(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ cls,
                  const uint8_t *__restrict__ band_rows, const typename Store<S>::R *__restrict__ c2f, int nx, int ny,
                  int nz, long long ncell, typename Store<S>::R c0sq, typename Store<S>::R cpsq, int H, int nslab,
                  int zc, int nseg, int *err) {
+    // rows of nx = V * W cells, V 16-byte vectors, split into nseg segments
+    // of up to 32 * CH vectors (the last one may be shorter; FULL: none is)
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -329,7 +332,11 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     // (cells xs .. xs + 32*W*CH - 1)
     const int row = warp / nseg, seg = warp % nseg;
     const int xs = seg * 32 * W * CH;
-    const bool whole = nseg == 1;  // one warp per row: x wraps by shuffles
+    const int vg = FULL ? 32 * CH : min(32 * CH, nx / W - seg * 32 * CH);  // vectors of this segment
+    const bool whole = nseg == 1 && vg == 32 * CH;  // one full warp per row: x wraps by shuffles
+    bool act[CH];                                   // slot holds cells
+#pragma unroll
+    for (int c = 0; c < CH; ++c) act[c] = FULL || c * 32 + lane < vg;
     const bool s1_row = row < rs;
     const bool s2_row = row >= 1 && row <= hs;
     const int y = (y0 - 1 + row + ny) % ny;
@@ -354,16 +361,23 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const int x0 = xs + (c * 32 + lane) * W;
+                if (act[c]) {
 #pragma unroll
-                for (int i = 0; i < 7; ++i) Vec<S>::ld(st + (size_t)i * rmax * rowel + x0, f[i][c]);
+                    for (int i = 0; i < 7; ++i) Vec<S>::ld(st + (size_t)i * rmax * rowel + x0, f[i][c]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 7; ++i)
+#pragma unroll
+                        for (int e = 0; e < W; ++e) f[i][c][e] = R(0);
+                }
                 // the c^2 the one-step kernels use for the class; a row without
                 // interface-band cells holds only fluid and object cells
-                const unsigned long long cl = load_classes<W>(clt + x0);
+                const unsigned long long cl = act[c] ? load_classes<W>(clt + x0) : 0ull;
                 if (band_row) {
 #pragma unroll
                     for (int e = 0; e < W; ++e) {
                         const unsigned kc = (unsigned)(cl >> (8 * e)) & 0xffu;
-                        cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : cst[x0 + e]);
+                        cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : (act[c] ? cst[x0 + e] : c0sq));
                     }
                 } else {
 #pragma unroll
@@ -375,10 +389,10 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
             R left = R(0), right = R(0);
             if (!whole) {
                 left = Vec<S>::get(st + (size_t)1 * rmax * rowel + (xs + nx - 1) % nx);
-                right = Vec<S>::get(st + (size_t)2 * rmax * rowel + (xs + 32 * W * CH) % nx);
+                right = Vec<S>::get(st + (size_t)2 * rmax * rowel + (xs + vg * W) % nx);
             }
             R fpx[CH][W], fmx[CH][W];
-            shift_x<R, CH, W>(f[1], f[2], lane, whole, left, right, fpx, fmx);
+            shift_x<R, CH, W>(f[1], f[2], lane, vg, whole, left, right, fpx, fmx);
             S *ry = ring + ((size_t)(k % kRingPlanes) * 2 * rmax + row) * rowel;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
@@ -399,14 +413,18 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
                 Vec<S>::rounded(o[6], c6v[c]);
                 const R (&oy)[W] = o[3];
                 const R (&omy)[W] = o[4];
-                Vec<S>::st(ry + x0, oy);                        // +y of row w
-                Vec<S>::st(ry + (size_t)rmax * rowel + x0, omy);  // -y of row w
+                if (act[c]) {
+                    Vec<S>::st(ry + x0, oy);                        // +y of row w
+                    Vec<S>::st(ry + (size_t)rmax * rowel + x0, omy);  // -y of row w
+                }
             }
             // the segment's end values for the neighbouring segments' S2
             if (!whole) {
                 R *ed = edge + ((size_t)(k % kRingPlanes) * rmax + row) * nseg * 2 + seg * 2;
-                if (lane == 31) ed[0] = c1v[CH - 1][W - 1];  // +x at the last cell
-                if (lane == 0) ed[1] = c2v[0][0];            // -x at the first cell
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    if (c * 32 + lane == vg - 1) ed[0] = c1v[c][W - 1];  // +x at the last cell
+                if (lane == 0) ed[1] = c2v[0][0];                        // -x at the first cell
             }
         }
         // stage `buf` consumed, ring plane k written; any failed wait ends the sweep
@@ -429,9 +447,10 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
                 right = ed[((seg + 1) % nseg) * 2 + 1];    // -x at the next segment's first cell
             }
             R fpx[CH][W], fmx[CH][W];
-            shift_x<R, CH, W>(n1, n2, lane, whole, left, right, fpx, fmx);
+            shift_x<R, CH, W>(n1, n2, lane, vg, whole, left, right, fpx, fmx);
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
+                if (!act[c]) continue;
                 const int x0 = xs + (c * 32 + lane) * W;
                 R fpy[W], fmy[W];
                 Vec<S>::ld(ry + (size_t)(row - 1) * rowel + x0, fpy);             // +y of row w-1
@@ -470,21 +489,21 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     }
 }
 
-// 16-byte vectors per lane across a whole row, or 0 if a row is not a whole
-// number of warp-wide vectors.
+// 16-byte vectors in a row, or 0 if a row is not a whole number of them or
+// its class bytes are not a whole number of 16-byte units (bulk copies).
 template <typename S>
 int row_vectors(const Geometry &g) {
     constexpr int W = Store<S>::W;
-    return g.n[0] % (32 * W) ? 0 : g.n[0] / (32 * W);
+    return (g.n[0] % W || g.n[0] % 16) ? 0 : g.n[0] / W;
 }
 
-// Chunks per lane for a row of v vectors per lane: two where they divide the
-// row and fit the registers (mode 3 asks for two), one with mode 2.
+// Chunks per lane for a row of V vectors: two where whole warps of two fill
+// the row and fit the registers (mode 3 asks for two), else one (mode 2).
 template <typename S>
-int chunks_for(int v, int mode) {
-    const bool two_fit = Store<S>::W * 2 <= 8 && v % 2 == 0;
+int chunks_for(int V, int mode) {
+    const bool two_fit = Store<S>::W * 2 <= 8 && V % 64 == 0;
     if (mode == 2) return 1;
-    if (mode == 3) return two_fit ? 2 : 0;
+    if (mode == 3) return Store<S>::W * 2 <= 8 ? 2 : 0;
     return two_fit ? 2 : 1;
 }
 
@@ -540,18 +559,22 @@ cudaError_t plan_ch(const Geometry &g, int want, int nseg, TwoStepPlan *pl) {
     pl->chunks_per_lane = CH;
     pl->threads = 32 * nseg * (pl->H + 2);
     pl->smem = per_row_all * (pl->H + 2) + fixed;
-    return cudaFuncSetAttribute(update2_slab<S, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
+    pl->full = (g.n[0] / Store<S>::W) % (32 * CH) == 0;
+    return pl->full ? cudaFuncSetAttribute(update2_slab<S, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)pl->smem)
+                    : cudaFuncSetAttribute(update2_slab<S, CH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)pl->smem);
 }
 
 // Chunks per lane and segments per row for `mode` (1: automatic, 2: one
 // chunk, 3: two), then the slab plan.
 template <typename S>
 cudaError_t plan_for(const Geometry &g, int want, int mode, TwoStepPlan *pl) {
-    const int v = row_vectors<S>(g);
-    const int ch = v ? chunks_for<S>(v, mode) : 0;
+    const int V = row_vectors<S>(g);
+    const int ch = V ? chunks_for<S>(V, mode) : 0;
     if (!ch) return cudaErrorInvalidValue;
-    if (ch == 1) return plan_ch<S, 1>(g, want, v, pl);
-    if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, v / 2, pl);
+    if (ch == 1) return plan_ch<S, 1>(g, want, (V + 31) / 32, pl);
+    if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, (V + 63) / 64, pl);
     return cudaErrorInvalidValue;
 }
 
@@ -576,7 +599,8 @@ cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl
         if (e == cudaSuccess && fork) e = cudaEventRecord(side.join, side.stream);
         if (e != cudaSuccess) return e;
     }
-    update2_slab<S, CH><<<pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(
+    auto kernel = pl.full ? update2_slab<S, CH, true> : update2_slab<S, CH, false>;
+    kernel<<<pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(
         (const S *)b.pop[src], (S *)b.pop[src ^ 1], b.cls, b.band_rows, (const R *)b.c2, g.n[0], g.n[1], g.n[2],
         g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp), pl.H, pl.nslab, pl.zc, pl.nseg, err);
     e = cudaGetLastError();

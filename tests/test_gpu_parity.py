@@ -339,6 +339,11 @@ def _two_step_outputs(wlb, prob, precision, settings, tail_steps=3, chunks_per_l
     ((384, 21, 32), 16.0, "f32", (0, 3), 0, 3),          # three one-chunk segments per row
     ((256, 40, 32), 16.0, "f16", (0, 2, 9), 0, 1),       # FP16 storage: t+1 rounded as stored
     ((512, 24, 32), 16.0, "f16", (0, 3), 0, 2),          # FP16, two warps per row
+    ((96, 24, 32), 16.0, "f32", (0, 5), 0, 1),           # ragged: one warp, 24 of 32 lanes
+    ((160, 24, 32), 16.0, "f32", (0, 3), 0, 2),          # ragged: 32 + 8 vectors in two warps
+    ((160, 21, 32), 16.0, "f32", (0, 4), 2, 1),          # ragged: one warp of two chunks, 40 of 64
+    ((208, 22, 32), 16.0, "f32", (0, 2), 1, 2),          # ragged: 32 + 20 vectors
+    ((160, 24, 32), 16.0, "f16", (0, 4), 0, 1),          # FP16 ragged: 20 of 32 lanes
 ])
 def test_two_step_is_bit_identical(wlb, shape, lam, precision, rows, cpl, segments):
     """Same per-cell arithmetic as two single steps: forces and fields equal bit
@@ -392,7 +397,7 @@ def test_two_step_rejected_where_unsupported(wlb):
                            n_periods=2, n_avg_periods=1)
     p3 = workloads.problem(3, (128, 32, 32), 2, 16.0, 3.0, (64.0, 16.0, 2.0), cp=0.42, n_surface=16,
                            n_periods=2, n_avg_periods=1)
-    p3odd = workloads.problem(3, (96, 32, 32), 2, 16.0, 3.0, (48.0, 16.0, 2.0), cp=0.42, n_surface=16,
+    p3odd = workloads.problem(3, (100, 32, 32), 2, 16.0, 3.0, (50.0, 16.0, 2.0), cp=0.42, n_surface=16,
                               n_periods=2, n_avg_periods=1)
     for prob, precision in ((p2, "f32"), (p3, "f64"), (p3odd, "f32")):
         with wlb.Solver(prob, precision=precision) as s:
