@@ -278,6 +278,10 @@ typedef struct {
     long long total_rows, total_points, max_steps;
     long long lattice_updates;      /* sum over lattices of cells x steps */
     int threads_per_block, blocks_per_sm, row_chunks;
+    int steps_per_launch;           /* 2: every launch advances all lattices two
+                                       steps (wlb_set_two_step's kernel, one
+                                       launch over every lattice's slabs)      */
+    int total_ctas;                 /* blocks of that launch, 0 if 1 step     */
 } wlb_batch_info;
 
 wlb_status wlb_batch_workspace_bytes(const wlb_params *ps, int count, size_t *bytes);
@@ -286,6 +290,14 @@ wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws
 wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tuning *best);
 wlb_status wlb_batch_run(wlb_batch *b, double *forces_out);
 wlb_status wlb_batch_get_info(const wlb_batch *b, wlb_batch_info *out);
+/* Steps two per launch for the whole batch: on by default when every lattice
+ * is 3D, periodic, FP32 or FP16 with rows the two-step kernel takes, and all
+ * run lengths, windows and periods are even; then one launch of the slab
+ * kernel covers every lattice (each with its own slab plan) and a batched
+ * sampling launch adds the sums of both steps.  Bit-identical to one step per
+ * launch.  enable = 0 returns to one step per launch; enable != 0 where the
+ * batch does not qualify gives WLB_ERR_ARG. */
+wlb_status wlb_batch_set_two_step(wlb_batch *b, int enable);
 const char *wlb_batch_last_error(const wlb_batch *b);
 wlb_status wlb_batch_destroy(wlb_batch *b);
 

@@ -71,7 +71,8 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int), ("total_rows", ctypes.c_longlong),
                 ("total_points", ctypes.c_longlong), ("max_steps", ctypes.c_longlong),
                 ("lattice_updates", ctypes.c_longlong), ("threads_per_block", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("row_chunks", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("row_chunks", ctypes.c_int),
+                ("steps_per_launch", ctypes.c_int), ("total_ctas", ctypes.c_int)]
 
 
 _lib = None
@@ -100,6 +101,7 @@ _SIGNATURES = {
     "wlb_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(BatchTuning)]),
     "wlb_batch_run": (ctypes.c_int, [_VP, _DP]),
     "wlb_batch_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(BatchInfo)]),
+    "wlb_batch_set_two_step": (ctypes.c_int, [_VP, ctypes.c_int]),
     "wlb_batch_last_error": (ctypes.c_char_p, [_VP]),
     "wlb_batch_destroy": (ctypes.c_int, [_VP]),
     "wlb_mlp_param_count": (ctypes.c_int, []),
@@ -309,6 +311,10 @@ class Batch:
         out = BatchInfo()
         self._bcheck(lib().wlb_batch_get_info(self._h, ctypes.byref(out)), "wlb_batch_get_info")
         return out
+
+    def set_two_step(self, enable=True):
+        """Two steps per launch for the whole batch (wlb_batch_set_two_step)."""
+        self._bcheck(lib().wlb_batch_set_two_step(self._h, 1 if enable else 0), "wlb_batch_set_two_step")
 
     def autotune(self, steps_per_trial=16):
         t = BatchTuning()

@@ -19,12 +19,6 @@
 namespace wlb {
 namespace {
 
-struct BatchLat {
-    Geometry g;
-    Buffers b;
-    long long n_steps, window_begin, period;
-};
-
 // What the update of one row needs, in 64 bytes.
 struct __align__(16) LatHot {
     const void *pop0, *pop1;
@@ -213,7 +207,7 @@ __global__ void __launch_bounds__(256) batch_sample(const BatchLat *__restrict__
                 double *a64 = L.b.acc64 + 5 * (long long)k;
                 bool bad = false;
                 for (int j = 0; j < 5; ++j) {
-                    const double v = a64[j] + (double)a[j] * scale;
+                    const double v = fold_value(a64[j], (double)a[j], scale);
                     a64[j] = v;
                     a[j] = R(0);
                     bad |= !isfinite(v);
@@ -268,7 +262,13 @@ struct wlb_batch {
     double *host_out = nullptr;  // count * 5 doubles (force[4] + flag)
     int threads = 256, blocks_per_sm = 4;
     cudaGraphExec_t graph = nullptr;
-    int graph_threads = 0, graph_bps = 0;
+    int graph_threads = 0, graph_bps = 0, graph_two = -1;
+    // two steps per launch (all lattices 3D periodic FP32/FP16 with even step
+    // counts): one launch of the slab kernel over every lattice's CTAs
+    bool two_ok = false, two = false, two_full = false;
+    int two_threads = 0, total_ctas = 0;
+    size_t two_smem = 0;
+    int *d_cta_lat = nullptr, *d_cta_first = nullptr;
     char err[512] = {0};
 };
 
@@ -322,6 +322,8 @@ size_t batch_layout(const wlb_params *ps, int count, char *base, std::vector<Bat
     for (int i = 0; i < count; ++i)
         if (ps[i].n_avg_periods > 0) total_points += ps[i].n_surface;
     off += align256(sizeof(int) * (total_points > 0 ? total_points : 1));  // point -> lattice
+    // two-step CTA -> lattice (at most one CTA per row) and each lattice's first CTA
+    off += align256(sizeof(int) * total_rows) + align256(sizeof(int) * (count + 1));
     return off;
 }
 
@@ -339,6 +341,17 @@ wlb_status batch_validate(const wlb_params *ps, int count) {
 
 cudaError_t issue_steps(wlb_batch *b, int nsteps, int threads, int bps, cudaStream_t s) {
     const int grid = b->n_sm * bps;
+    if (b->two) {  // step counts are even in this mode
+        if (nsteps % 2) return cudaErrorInvalidValue;
+        for (int k = 0; k < nsteps; k += 2) {
+            cudaError_t e = wlb::launch_batch_two_steps(b->prec, b->two_full, b->d_lats, b->d_cta_lat,
+                                                        b->d_cta_first, b->total_ctas, b->two_threads, b->two_smem,
+                                                        b->d_pt_lat, b->d_pt_begin, b->total_points, b->d_step,
+                                                        b->d_done, grid, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     for (int k = 0; k < nsteps; ++k) {
         cudaError_t e;
         if (b->total_points > 0) {
@@ -470,9 +483,13 @@ wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws
     }
     int *row_lat_base = (int *)tb;
     {
-        long long tr = 0;
+        long long tr = 0, tp = 0;
         for (int i = 0; i < count; ++i) tr += (long long)ps[i].ny * ps[i].nz;
+        for (int i = 0; i < count; ++i)
+            if (ps[i].n_avg_periods > 0) tp += ps[i].n_surface;
         b->d_pt_lat = (int *)(tb + align256(sizeof(int) * tr));
+        b->d_cta_lat = (int *)((char *)b->d_pt_lat + align256(sizeof(int) * (tp > 0 ? tp : 1)));
+        b->d_cta_first = (int *)((char *)b->d_cta_lat + align256(sizeof(int) * tr));
     }
     std::vector<long long> rows(count + 1), pts(count + 1);
     int maxv = 1;
@@ -546,6 +563,25 @@ wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws
         if (e == cudaSuccess)
             e = cudaMemcpy(b->d_class_row_lat[k], rl.data(), sizeof(int) * rl.size(), cudaMemcpyHostToDevice);
     }
+    // two steps per launch where every lattice takes it (plans land in b->lat)
+    bool even = b->dim == 3;
+    for (int i = 0; i < count && even; ++i)
+        even = b->lat[i].n_steps % 2 == 0 && b->lat[i].window_begin % 2 == 0 && b->lat[i].period % 2 == 0;
+    if (even && wlb::plan_batch_two_steps(b->prec, b->lat.data(), count, &b->two_threads, &b->two_smem, &b->two_full)) {
+        std::vector<int> first(count + 1, 0), owner;
+        for (int i = 0; i < count; ++i) {
+            const int n = b->lat[i].plan.nslab * b->lat[i].plan.chunks;
+            first[i + 1] = first[i] + n;
+            owner.insert(owner.end(), (size_t)n, i);
+        }
+        b->total_ctas = first[count];
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_cta_lat, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_cta_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice);
+        b->two_ok = b->two = true;
+    }
+    cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(b->d_lats, b->lat.data(), sizeof(BatchLat) * count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_pt_lat, pl.data(), sizeof(int) * pl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_row_begin, rows.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice);
@@ -567,6 +603,26 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
     cudaEvent_t e0, e1;
     BATCH_CUDA(b, cudaEventCreate(&e0), "event");
     BATCH_CUDA(b, cudaEventCreate(&e1), "event");
+    if (b->two) {  // the two-step launch has its own plan: time it, nothing to choose
+        const int steps = 2 * ((steps_per_trial + 1) / 2);
+        cudaError_t e = issue_steps(b, 2, b->threads, b->blocks_per_sm, b->stream);  // warm up
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(long long), b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = issue_steps(b, steps, b->threads, b->blocks_per_sm, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess) return bfail(b, WLB_ERR_CUDA, "autotune trial", e);
+        if (best) {
+            best->threads_per_block = b->two_threads;
+            best->blocks_per_sm = 1;
+            best->ms_per_step = ms / steps;
+        }
+        return WLB_OK;
+    }
     const int threads_c[] = {128, 256};
     const int bps_c[] = {2, 4, 8, 16};
     float best_ms = 1e30f;
@@ -605,7 +661,8 @@ wlb_status wlb_batch_run(wlb_batch *b, double *forces_out) {
     if (!b || !forces_out) return WLB_ERR_ARG;
     wlb_status st = batch_setup(b);
     if (st != WLB_OK) return st;
-    if (!b->graph || b->graph_threads != b->threads || b->graph_bps != b->blocks_per_sm) {
+    if (!b->graph || b->graph_threads != b->threads || b->graph_bps != b->blocks_per_sm ||
+        b->graph_two != (int)b->two) {
         if (b->graph) cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
         BATCH_CUDA(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -624,6 +681,7 @@ wlb_status wlb_batch_run(wlb_batch *b, double *forces_out) {
         }
         b->graph_threads = b->threads;
         b->graph_bps = b->blocks_per_sm;
+        b->graph_two = (int)b->two;
     }
     const long long full = b->max_steps / wlb::kGraphSteps, rest = b->max_steps % wlb::kGraphSteps;
     for (long long k = 0; k < full; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
@@ -663,6 +721,15 @@ wlb_status wlb_batch_get_info(const wlb_batch *b, wlb_batch_info *out) {
     out->threads_per_block = b->threads;
     out->blocks_per_sm = b->blocks_per_sm;
     out->row_chunks = b->chunks;
+    out->steps_per_launch = b->two ? 2 : 1;
+    out->total_ctas = b->two ? b->total_ctas : 0;
+    return WLB_OK;
+}
+
+wlb_status wlb_batch_set_two_step(wlb_batch *b, int enable) {
+    if (!b) return WLB_ERR_ARG;
+    if (enable && !b->two_ok) return bfail(b, WLB_ERR_ARG, "two steps per launch not available for this batch");
+    b->two = enable != 0;
     return WLB_OK;
 }
 

@@ -98,4 +98,26 @@ struct SideStream {
 cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src, bool sample,
                              int *err, cudaStream_t s, const SideStream &side);
 
+// One lattice of a batched ensemble (wlb_batch.cu): geometry, buffers, its
+// protocol lengths and, when the batch runs two steps per launch, its plan.
+struct BatchLat {
+    Geometry g;
+    Buffers b;
+    long long n_steps, window_begin, period;
+    TwoStepPlan plan;
+};
+
+// Batched two steps per launch: plan every lattice (one 16-byte chunk per
+// lane), returning the launch's block size and shared memory and whether all
+// rows are full warps; false if some lattice cannot take it.
+bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, int *threads, size_t *smem, bool *full);
+// One launch of two steps for every active lattice: CTA j works on lattice
+// cta_lat[j] (its CTA j - cta_first[lattice]); with points, a sampling launch
+// before it adds the sums of both steps.  The state at step t is in buffer
+// (t / 2) & 1; the last CTA advances *step by 2.
+cudaError_t launch_batch_two_steps(Prec p, bool full, const BatchLat *lats, const int *cta_lat, const int *cta_first,
+                                   int total_ctas, int threads, size_t smem, const int *pt_lat,
+                                   const long long *pt_begin, long long total_points, long long *step,
+                                   unsigned *done, int sample_grid, cudaStream_t s);
+
 }  // namespace wlb

@@ -197,6 +197,12 @@ inline SampleArgs<S> sample_args(const Geometry &g, const Buffers &b) {
     return a;
 }
 
+// End-of-period fold of one running sum into its FP64 total (scale converts
+// stored units back), explicit rounding: acc64 + acc * scale as one FMA.
+__device__ __forceinline__ double fold_value(double acc64, double acc, double scale) {
+    return fma_rn(acc, scale, acc64);
+}
+
 // acc += (P^2, U.U, U_x (U.n), U_y (U.n), U_z (U.n)), explicit rounding.
 template <typename R>
 __device__ __forceinline__ void accumulate_point(R *acc, R p, const R (&u)[3], const R *n) {
@@ -208,17 +214,17 @@ __device__ __forceinline__ void accumulate_point(R *acc, R p, const R (&u)[3], c
     acc[4] = fma_rn(u[2], un, acc[4]);
 }
 
-template <typename S, typename M>
-__device__ __forceinline__ void sample_point_with(const SampleArgs<S> &a, int k, int lane, M moments) {
-    using R = typename Store<S>::R;
-    const Geometry &g = a.g;
+template <typename R, typename M>
+__device__ __forceinline__ void sample_point_with(const Geometry &g, const int4 *__restrict__ st_xyz,
+                                                  const R *__restrict__ st_w, const R *__restrict__ nrm, R *acc, int k,
+                                                  int lane, M moments) {
     R p = R(0), u[3] = {R(0), R(0), R(0)};
     if (lane < g.stencil) {
         const long long o = (long long)k * g.stencil + lane;
-        const int4 c = a.st_xyz[o];
+        const int4 c = st_xyz[o];
         R rho, J[3];
         moments(c.x, c.y, c.z, rho, J);
-        const R wp = a.st_w[2 * o], wu = a.st_w[2 * o + 1];
+        const R wp = st_w[2 * o], wu = st_w[2 * o + 1];
         p = wp * rho;
         u[0] = wu * J[0];
         u[1] = wu * J[1];
@@ -231,7 +237,12 @@ __device__ __forceinline__ void sample_point_with(const SampleArgs<S> &a, int k,
         u[1] += __shfl_xor_sync(kFull, u[1], m);
         u[2] += __shfl_xor_sync(kFull, u[2], m);
     }
-    if (lane == 0) accumulate_point(a.acc + 5 * (long long)k, p, u, a.nrm + 4 * (long long)k);
+    if (lane == 0) accumulate_point(acc + 5 * (long long)k, p, u, nrm + 4 * (long long)k);
+}
+
+template <typename S, typename M>
+__device__ __forceinline__ void sample_point_with(const SampleArgs<S> &a, int k, int lane, M moments) {
+    sample_point_with(a.g, a.st_xyz, a.st_w, a.nrm, a.acc, k, lane, moments);
 }
 
 // Driven-cavity parameters of one step (Sec. VII).

@@ -190,7 +190,7 @@ __global__ void fold_sums(int n, R *__restrict__ acc, double *__restrict__ acc64
                           int *__restrict__ err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double v = acc64[i] + (double)acc[i] * scale;
+    const double v = fold_value(acc64[i], (double)acc[i], scale);
     acc64[i] = v;
     acc[i] = R(0);
     if (!isfinite(v)) atomicExch(err, 1);

@@ -239,17 +239,37 @@ __global__ void __launch_bounds__(256) sample_two(SampleArgs<S> a, const S *__re
     });
 }
 
+// One lattice as a two-step CTA sees it.
+template <typename S>
+struct SlabParams {
+    const S *A;  // state t
+    S *B;        // state t + 2
+    const uint8_t *cls, *band_rows;
+    const typename Store<S>::R *c2f;
+    int nx, ny, nz;
+    long long ncell;
+    typename Store<S>::R c0sq, cpsq;
+    int H, nslab, zc, nseg;  // plan
+    int *err;
+};
+
+// The sweep of CTA `cta` of a lattice (slab cta % nslab, z-chunk cta / nslab)
+// in the dynamic shared memory `smem`.  Block-uniform control flow.
 template <typename S, int CH, bool FULL>
-__global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
-    update2_slab(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ cls,
-                 const uint8_t *__restrict__ band_rows, const typename Store<S>::R *__restrict__ c2f, int nx, int ny,
-                 int nz, long long ncell, typename Store<S>::R c0sq, typename Store<S>::R cpsq, int H, int nslab,
-                 int zc, int nseg, int *err) {
+__device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsigned char *smem) {
     // rows of nx = V * W cells, V 16-byte vectors, split into nseg segments
     // of up to 32 * CH vectors (the last one may be shorter; FULL: none is)
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
-    extern __shared__ __align__(128) unsigned char smem[];
+    const S *__restrict__ A = P.A;
+    S *__restrict__ B = P.B;
+    const uint8_t *__restrict__ cls = P.cls;
+    const uint8_t *__restrict__ band_rows = P.band_rows;
+    const R *__restrict__ c2f = P.c2f;
+    const int nx = P.nx, ny = P.ny, nz = P.nz, H = P.H, nslab = P.nslab, zc = P.zc, nseg = P.nseg;
+    const long long ncell = P.ncell;
+    const R c0sq = P.c0sq, cpsq = P.cpsq;
+    int *err = P.err;
     const int rmax = H + 2;
     const size_t rowel = (size_t)nx;
     S *stage = reinterpret_cast<S *>(smem);                                          // [kStages][7][rmax][nx]
@@ -260,7 +280,7 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     uint64_t *bar = reinterpret_cast<uint64_t *>(edge + (size_t)kRingPlanes * rmax * nseg * 2);  // [kStages]
     uint8_t *rowflag = reinterpret_cast<uint8_t *>(bar + kStages);  // [kStages][rmax]: row holds band cells
 
-    const int slab = blockIdx.x % nslab, chunk = blockIdx.x / nslab;
+    const int slab = cta % nslab, chunk = cta / nslab;
     const int y0 = slab * H;
     const int hs = min(H, ny - y0);  // rows of this slab
     const int rs = hs + 2;           // S1 rows
@@ -489,6 +509,102 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     }
 }
 
+template <typename S, int CH, bool FULL>
+__global__ void __launch_bounds__(two_step_threads<S, CH>(), 1) update2_slab(SlabParams<S> P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    slab_body<S, CH, FULL>(P, blockIdx.x, smem);
+}
+
+// Batched ensembles: CTA j sweeps CTA j - cta_first[i] of lattice
+// i = cta_lat[j] (each lattice with its own plan), skipping lattices past
+// their n_steps.  Every launch is two steps, so the state at step t is in
+// buffer (t / 2) & 1.  The last CTA to finish advances the step: every CTA
+// has read it by then.
+template <typename S, int CH, bool FULL>
+__global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
+    batch_update2(const BatchLat *__restrict__ lats, const int *__restrict__ cta_lat,
+                  const int *__restrict__ cta_first, long long *step, unsigned *done) {
+    using R = typename Store<S>::R;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const long long t = *step;
+    const int i = cta_lat[blockIdx.x];
+    const BatchLat &L = lats[i];
+    if (t < L.n_steps) {  // block-uniform
+        const int src = (int)((t >> 1) & 1);
+        SlabParams<S> P;
+        P.A = (const S *)L.b.pop[src];
+        P.B = (S *)L.b.pop[src ^ 1];
+        P.cls = L.b.cls;
+        P.band_rows = L.b.band_rows;
+        P.c2f = (const R *)L.b.c2;
+        P.nx = L.g.n[0];
+        P.ny = L.g.n[1];
+        P.nz = L.g.n[2];
+        P.ncell = L.g.ncell;
+        P.c0sq = (R)(L.g.c0 * L.g.c0);
+        P.cpsq = (R)(L.g.cp * L.g.cp);
+        P.H = L.plan.H;
+        P.nslab = L.plan.nslab;
+        P.zc = L.plan.zc;
+        P.nseg = L.plan.nseg;
+        P.err = L.b.err;
+        slab_body<S, CH, FULL>(P, blockIdx.x - cta_first[i], smem);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(done, 1u);
+        if (ticket == gridDim.x - 1) {
+            *done = 0;
+            *step = t + 2;
+            __threadfence();
+        }
+    }
+}
+
+// Batched sampling of both steps of a launch: grid-stride over all points;
+// warps of lattices outside their window skip.  Sums of t (stored state) and
+// t+1 (recomputed, moments_next) in that order, then the period fold by the
+// point's lane 0 when t+1 closes a period (periods and windows are even).
+template <typename S>
+__global__ void __launch_bounds__(256) batch_sample_two(const BatchLat *__restrict__ lats,
+                                                        const int *__restrict__ pt_lat,
+                                                        const long long *__restrict__ pt_begin,
+                                                        long long total_points, const long long *step) {
+    using R = typename Store<S>::R;
+    const long long t = *step;
+    const int lane = threadIdx.x & 31;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < total_points; p += warps) {
+        const int i = pt_lat[p];
+        const BatchLat &L = lats[i];
+        if (t < L.window_begin || t >= L.n_steps) continue;  // uniform per warp
+        const int k = (int)(p - pt_begin[i]);
+        const S *A = (const S *)L.b.pop[(t >> 1) & 1];
+        const R *st_w = (const R *)L.b.st_w, *nrm = (const R *)L.b.nrm;
+        R *accs = (R *)L.b.acc;
+        sample_point_with(L.g, L.b.st_xyz, st_w, nrm, accs, k, lane, [&](int x, int y, int z, R &rho, R(&J)[3]) {
+            pulled_moments(L.g, A, x, y, z, rho, J);
+        });
+        sample_point_with(L.g, L.b.st_xyz, st_w, nrm, accs, k, lane, [&](int x, int y, int z, R &rho, R(&J)[3]) {
+            moments_next(L.g, A, (const R *)L.b.c2, x, y, z, rho, J);
+        });
+        if (lane == 0 && (t + 2 - L.window_begin) % L.period == 0) {
+            const double scale = 1.0 / (L.g.pop_scale * L.g.pop_scale);
+            R *acc = accs + 5 * (long long)k;
+            double *a64 = L.b.acc64 + 5 * (long long)k;
+            bool bad = false;
+            for (int j = 0; j < 5; ++j) {
+                const double v = fold_value(a64[j], (double)acc[j], scale);
+                a64[j] = v;
+                acc[j] = R(0);
+                bad |= !isfinite(v);
+            }
+            if (bad) atomicExch(L.b.err, 1);
+        }
+    }
+}
+
 // 16-byte vectors in a row, or 0 if a row is not a whole number of them or
 // its class bytes are not a whole number of 16-byte units (bulk copies).
 template <typename S>
@@ -560,10 +676,12 @@ cudaError_t plan_ch(const Geometry &g, int want, int nseg, TwoStepPlan *pl) {
     pl->threads = 32 * nseg * (pl->H + 2);
     pl->smem = per_row_all * (pl->H + 2) + fixed;
     pl->full = (g.n[0] / Store<S>::W) % (32 * CH) == 0;
+    // the attribute belongs to the kernel, shared by every handle: allow the
+    // device's whole opt-in shared memory, not just this plan's
     return pl->full ? cudaFuncSetAttribute(update2_slab<S, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)pl->smem)
+                                           smem_max)
                     : cudaFuncSetAttribute(update2_slab<S, CH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)pl->smem);
+                                           smem_max);
 }
 
 // Chunks per lane and segments per row for `mode` (1: automatic, 2: one
@@ -580,6 +698,29 @@ cudaError_t plan_for(const Geometry &g, int want, int mode, TwoStepPlan *pl) {
 
 // The sampling kernel runs in 128-thread blocks so that one fits on an SM
 // beside a two-step CTA (registers), and on the SMs the grid leaves free.
+template <typename S>
+SlabParams<S> slab_params(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, int *err) {
+    using R = typename Store<S>::R;
+    SlabParams<S> P;
+    P.A = (const S *)b.pop[src];
+    P.B = (S *)b.pop[src ^ 1];
+    P.cls = b.cls;
+    P.band_rows = b.band_rows;
+    P.c2f = (const R *)b.c2;
+    P.nx = g.n[0];
+    P.ny = g.n[1];
+    P.nz = g.n[2];
+    P.ncell = g.ncell;
+    P.c0sq = (R)(g.c0 * g.c0);
+    P.cpsq = (R)(g.cp * g.cp);
+    P.H = pl.H;
+    P.nslab = pl.nslab;
+    P.zc = pl.zc;
+    P.nseg = pl.nseg;
+    P.err = err;
+    return P;
+}
+
 template <typename S, int CH>
 cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, bool sample, int *err,
                       cudaStream_t s, const SideStream &side) {
@@ -600,9 +741,7 @@ cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl
         if (e != cudaSuccess) return e;
     }
     auto kernel = pl.full ? update2_slab<S, CH, true> : update2_slab<S, CH, false>;
-    kernel<<<pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(
-        (const S *)b.pop[src], (S *)b.pop[src ^ 1], b.cls, b.band_rows, (const R *)b.c2, g.n[0], g.n[1], g.n[2],
-        g.ncell, (R)(g.c0 * g.c0), (R)(g.cp * g.cp), pl.H, pl.nslab, pl.zc, pl.nseg, err);
+    kernel<<<pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(slab_params<S>(g, b, pl, src, err));
     e = cudaGetLastError();
     if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(s, side.join, 0);  // the next launch overwrites src
     return e;
@@ -645,6 +784,98 @@ cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const 
     switch (p) {
         case Prec::F16: return launch_for<__half>(g, b, pl, src, sample, err, s, side);
         case Prec::F32: return launch_for<float>(g, b, pl, src, sample, err, s, side);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+namespace {
+
+template <typename S>
+bool plan_batch_for(BatchLat *lats, int count, int *threads, size_t *smem, bool *full) {
+    using R = typename Store<S>::R;
+    int dev = 0, smem_max = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    const size_t fixed = kStages * sizeof(uint64_t) + kStages * (size_t)kMaxRows + 16;
+    int t_max = 0;
+    size_t s_max = 0;
+    bool all_full = true;
+    for (int i = 0; i < count; ++i) {
+        const Geometry &g = lats[i].g;
+        const int V = row_vectors<S>(g);
+        if (g.dim != 3 || g.driven || !V) return false;
+        const int nseg = (V + 31) / 32;
+        const size_t per_row = smem_per_row((size_t)g.n[0] * sizeof(S), (size_t)g.n[0] * sizeof(R), (size_t)g.n[0]) +
+                               (size_t)kRingPlanes * nseg * 2 * sizeof(R);
+        int rows = (int)(((size_t)smem_max - fixed) / per_row);
+        rows = std::min(rows, two_step_threads<S, 1>() / (32 * nseg));
+        if (rows < 3) return false;
+        TwoStepPlan pl;
+        pl.H = std::min(rows - 2, g.n[1]);
+        pl.nslab = (g.n[1] + pl.H - 1) / pl.H;
+        // z-chunks of about 32 planes: many CTAs of similar work across lattices
+        pl.chunks = (g.n[2] + 31) / 32;
+        pl.zc = (g.n[2] + pl.chunks - 1) / pl.chunks;
+        pl.chunks = (g.n[2] + pl.zc - 1) / pl.zc;
+        pl.nseg = nseg;
+        pl.chunks_per_lane = 1;
+        pl.threads = 32 * nseg * (pl.H + 2);
+        pl.smem = per_row * (pl.H + 2) + fixed;
+        pl.full = V % 32 == 0;
+        lats[i].plan = pl;
+        t_max = std::max(t_max, pl.threads);
+        s_max = std::max(s_max, pl.smem);
+        all_full = all_full && pl.full;
+    }
+    // shared by every batch: the device's whole opt-in shared memory
+    cudaError_t e = all_full ? cudaFuncSetAttribute(batch_update2<S, 1, true>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)
+                             : cudaFuncSetAttribute(batch_update2<S, 1, false>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (e != cudaSuccess) return false;
+    *threads = t_max;
+    *smem = s_max;
+    *full = all_full;
+    return true;
+}
+
+template <typename S>
+cudaError_t launch_batch_for(bool full, const BatchLat *lats, const int *cta_lat, const int *cta_first,
+                             int total_ctas, int threads, size_t smem, const int *pt_lat, const long long *pt_begin,
+                             long long total_points, long long *step, unsigned *done, int sample_grid,
+                             cudaStream_t s) {
+    if (total_points > 0) {
+        batch_sample_two<S><<<sample_grid, 256, 0, s>>>(lats, pt_lat, pt_begin, total_points, step);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    auto kernel = full ? batch_update2<S, 1, true> : batch_update2<S, 1, false>;
+    kernel<<<total_ctas, threads, smem, s>>>(lats, cta_lat, cta_first, step, done);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, int *threads, size_t *smem, bool *full) {
+    switch (p) {
+        case Prec::F16: return plan_batch_for<__half>(lats, count, threads, smem, full);
+        case Prec::F32: return plan_batch_for<float>(lats, count, threads, smem, full);
+        default: return false;
+    }
+}
+
+cudaError_t launch_batch_two_steps(Prec p, bool full, const BatchLat *lats, const int *cta_lat, const int *cta_first,
+                                   int total_ctas, int threads, size_t smem, const int *pt_lat,
+                                   const long long *pt_begin, long long total_points, long long *step,
+                                   unsigned *done, int sample_grid, cudaStream_t s) {
+    switch (p) {
+        case Prec::F16:
+            return launch_batch_for<__half>(full, lats, cta_lat, cta_first, total_ctas, threads, smem, pt_lat,
+                                            pt_begin, total_points, step, done, sample_grid, s);
+        case Prec::F32:
+            return launch_batch_for<float>(full, lats, cta_lat, cta_first, total_ctas, threads, smem, pt_lat,
+                                           pt_begin, total_points, step, done, sample_grid, s);
         default: return cudaErrorInvalidValue;
     }
 }

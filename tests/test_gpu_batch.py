@@ -85,6 +85,52 @@ def test_batch_autotune_and_member_without_window(wlb):
     assert abs(F[0, 2] - Fs[2]) <= 1e-6 * abs(Fs[2])
 
 
+def _members_two_step(precision="f32"):
+    # rows of 96, 64, 160 and 128 cells (multiples of 16: two steps per launch),
+    # uneven periods and run lengths, one member without an averaging window
+    specs = [((96, 24, 32), 16.0, 3.0, 20, 5), ((64, 24, 24), 24.0, 3.5, 12, 4),
+             ((160, 24, 32), 32.0, 3.0, 6, 2), ((128, 40, 32), 16.0, 4.0, 16, 0)]
+    out = []
+    for i, (n, lam, R, per, avg) in enumerate(specs):
+        c = (n[0] / 2 + 0.25, n[1] / 2 - 0.5, lam / 8 + 0.125 * i)
+        out.append(workloads.problem(3, n, 2, lam, R, c, cp=0.25 * (0.8 + 0.3 * i), n_surface=100 + 50 * i,
+                                     n_periods=per, n_avg_periods=avg, precision=precision))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_batch_two_steps_per_launch_bit_identical(wlb, precision):
+    """The batched two-step launch (one slab launch over every lattice, batched
+    sampling of both steps) gives the same bits as one step per launch and as
+    every lattice run alone."""
+    probs = _members_two_step(precision)
+    with wlb.Batch(probs) as b:
+        info = b.info()
+        assert info.steps_per_launch == 2 and info.total_ctas > 0
+        F2 = b.run()
+        b.set_two_step(False)
+        assert b.info().steps_per_launch == 1
+        F1 = b.run()
+        b.set_two_step(True)
+        best = b.autotune(steps_per_trial=8)
+        assert best["blocks_per_sm"] == 1 and best["ms_per_step"] > 0
+        F2b = b.run()
+    assert np.array_equal(F2, F1) and np.array_equal(F2, F2b)
+    assert np.array_equal(F2[3], np.zeros(3))  # no averaging window
+    for i, p in enumerate(probs[:3]):
+        with wlb.Solver(p) as s:
+            Fs = s.run()
+        assert np.array_equal(F2[i], Fs), (i, F2[i], Fs)
+
+
+def test_batch_two_step_unavailable(wlb):
+    probs = _members_3d()  # a 40-cell row: not a whole number of 16 cells
+    with wlb.Batch(probs) as b:
+        assert b.info().steps_per_launch == 1
+        with pytest.raises(wlb.WlbError):
+            b.set_two_step(True)
+
+
 def test_batch_rejects_mixed_or_unsupported(wlb):
     p3 = _members_3d()[0]
     p2 = workloads.problem(2, (48, 32), 1, 16.0, 3.0, (24.0, 2.0), cp=0.3, n_surface=8,

@@ -379,6 +379,25 @@ def test_two_step_odd_period_and_split_calls(wlb):
         assert np.array_equal(a, b)
 
 
+def test_two_step_handles_with_different_plans_coexist(wlb):
+    """Plans of different shared-memory size created before any runs: each
+    handle still launches (the kernel's shared-memory limit is not the last
+    plan's), and each matches its single-step force."""
+    shapes = [(96, 24, 32), (160, 24, 32), (128, 40, 32)]
+    probs = [workloads.problem(3, n, 2, 16.0, 3.0, (n[0] / 2 + 0.25, n[1] / 2 - 0.5, 2.0), cp=0.42,
+                               n_surface=60, n_periods=4, n_avg_periods=1) for n in shapes]
+    solvers = [wlb.Solver(p) for p in probs]
+    try:
+        F = [s.run() for s in solvers]
+    finally:
+        for s in solvers:
+            s.close()
+    for p, f in zip(probs, F):
+        with wlb.Solver(p) as s:
+            s.set_two_step(False)
+            assert np.array_equal(s.run(), f)
+
+
 def test_two_step_benchmark_lattice(wlb):
     """256^3 benchmark lattice, full protocol: identical force with and without,
     FP32 and FP16 storage."""
