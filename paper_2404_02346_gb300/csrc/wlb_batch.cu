@@ -179,29 +179,11 @@ __global__ void __launch_bounds__(256) batch_sample(const BatchLat *__restrict__
         if (t < L.window_begin || t >= L.n_steps) continue;  // uniform per warp
         const int k = (int)(p - pt_begin[i]);
         const S *src = (const S *)L.b.pop[t & 1];
-        R pv = R(0), u[3] = {R(0), R(0), R(0)};
-        if (lane < L.g.stencil) {
-            const long long o = (long long)k * L.g.stencil + lane;
-            const int4 c = L.b.st_xyz[o];
-            R rho, J[3];
-            pulled_moments(L.g, src, c.x, c.y, c.z, rho, J);
-            const R *w = (const R *)L.b.st_w;
-            const R wp = w[2 * o], wu = w[2 * o + 1];
-            pv = wp * rho;
-            u[0] = wu * J[0];
-            u[1] = wu * J[1];
-            u[2] = wu * J[2];
-        }
-#pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) {
-            pv += __shfl_xor_sync(kFull, pv, m);
-            u[0] += __shfl_xor_sync(kFull, u[0], m);
-            u[1] += __shfl_xor_sync(kFull, u[1], m);
-            u[2] += __shfl_xor_sync(kFull, u[2], m);
-        }
+        R *acc = (R *)L.b.acc;
+        sample_point_with(L.g, L.b.st_xyz, (const R *)L.b.st_w, (const R *)L.b.nrm, acc, k, lane,
+                          [&](int x, int y, int z, R &rho, R(&J)[3]) { pulled_moments(L.g, src, x, y, z, rho, J); });
         if (lane == 0) {
-            R *a = (R *)L.b.acc + 5 * (long long)k;
-            accumulate_point(a, pv, u, (const R *)L.b.nrm + 4 * (long long)k);
+            R *a = acc + 5 * (long long)k;
             if ((t - L.window_begin + 1) % L.period == 0) {
                 const double scale = 1.0 / (L.g.pop_scale * L.g.pop_scale);
                 double *a64 = L.b.acc64 + 5 * (long long)k;
@@ -214,6 +196,44 @@ __global__ void __launch_bounds__(256) batch_sample(const BatchLat *__restrict__
                 }
                 if (bad) atomicExch(L.b.err, 1);
             }
+        }
+    }
+}
+
+// 2D lattices: one thread per point (the 3 x 3 stencil in registers) instead
+// of a warp, same sums (sample_point_2d_thread); grid-stride over all points,
+// fold at period ends as in batch_sample.
+template <typename S>
+__global__ void __launch_bounds__(256) batch_sample_2d(const BatchLat *__restrict__ lats,
+                                                       const int *__restrict__ pt_lat,
+                                                       const long long *__restrict__ pt_begin,
+                                                       long long total_points, const long long *step) {
+    using R = typename Store<S>::R;
+    const long long t = *step;
+    const long long threads = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < total_points; p += threads) {
+        const int i = pt_lat[p];
+        const BatchLat &L = lats[i];
+        if (t < L.window_begin || t >= L.n_steps) continue;
+        const int k = (int)(p - pt_begin[i]);
+        const S *src = (const S *)L.b.pop[t & 1];
+        R *a = (R *)L.b.acc;
+        sample_point_2d_thread(L.g, L.b.st_xyz, (const R *)L.b.st_w, (const R *)L.b.nrm, a, k,
+                               [&](int x, int y, int z, R &rho, R(&J)[3]) {
+                                   pulled_moments(L.g, src, x, y, z, rho, J);
+                               });
+        if ((t - L.window_begin + 1) % L.period == 0) {
+            const double scale = 1.0 / (L.g.pop_scale * L.g.pop_scale);
+            R *ak = a + 5 * (long long)k;
+            double *a64 = L.b.acc64 + 5 * (long long)k;
+            bool bad = false;
+            for (int j = 0; j < 5; ++j) {
+                const double v = fold_value(a64[j], (double)ak[j], scale);
+                a64[j] = v;
+                ak[j] = R(0);
+                bad |= !isfinite(v);
+            }
+            if (bad) atomicExch(L.b.err, 1);
         }
     }
 }
@@ -354,7 +374,25 @@ cudaError_t issue_steps(wlb_batch *b, int nsteps, int threads, int bps, cudaStre
     }
     for (int k = 0; k < nsteps; ++k) {
         cudaError_t e;
-        if (b->total_points > 0) {
+        if (b->total_points > 0 && b->dim == 2) {
+            const long long need = (b->total_points + threads - 1) / threads;
+            const int g2 = (int)(need < grid ? need : grid);
+            switch (b->prec) {
+                case wlb::Prec::F64:
+                    wlb::batch_sample_2d<double><<<g2, threads, 0, s>>>(b->d_lats, b->d_pt_lat, b->d_pt_begin,
+                                                                       b->total_points, b->d_step);
+                    break;
+                case wlb::Prec::F16:
+                    wlb::batch_sample_2d<__half><<<g2, threads, 0, s>>>(b->d_lats, b->d_pt_lat, b->d_pt_begin,
+                                                                       b->total_points, b->d_step);
+                    break;
+                default:
+                    wlb::batch_sample_2d<float><<<g2, threads, 0, s>>>(b->d_lats, b->d_pt_lat, b->d_pt_begin,
+                                                                      b->total_points, b->d_step);
+                    break;
+            }
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        } else if (b->total_points > 0) {
             switch (b->prec) {
                 case wlb::Prec::F64:
                     wlb::batch_sample<double><<<grid, threads, 0, s>>>(b->d_lats, b->d_pt_lat, b->d_pt_begin,

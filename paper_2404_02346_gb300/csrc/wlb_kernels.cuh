@@ -225,19 +225,48 @@ __device__ __forceinline__ void sample_point_with(const Geometry &g, const int4 
         R rho, J[3];
         moments(c.x, c.y, c.z, rho, J);
         const R wp = st_w[2 * o], wu = st_w[2 * o + 1];
-        p = wp * rho;
-        u[0] = wu * J[0];
-        u[1] = wu * J[1];
-        u[2] = wu * J[2];
+        p = mul_rn(wp, rho);
+        u[0] = mul_rn(wu, J[0]);
+        u[1] = mul_rn(wu, J[1]);
+        u[2] = mul_rn(wu, J[2]);
     }
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
-        p += __shfl_xor_sync(kFull, p, m);
-        u[0] += __shfl_xor_sync(kFull, u[0], m);
-        u[1] += __shfl_xor_sync(kFull, u[1], m);
-        u[2] += __shfl_xor_sync(kFull, u[2], m);
+        p = add_rn(p, __shfl_xor_sync(kFull, p, m));
+        u[0] = add_rn(u[0], __shfl_xor_sync(kFull, u[0], m));
+        u[1] = add_rn(u[1], __shfl_xor_sync(kFull, u[1], m));
+        u[2] = add_rn(u[2], __shfl_xor_sync(kFull, u[2], m));
     }
     if (lane == 0) accumulate_point(acc + 5 * (long long)k, p, u, nrm + 4 * (long long)k);
+}
+
+// The same for a 2D point (3 x 3 stencil) by one thread: the nine terms are
+// summed in the order the xor-butterfly above sums lanes 0..8 (the other
+// lanes add exact zeros): [((v0 + v8) + v4) + (v2 + v6)] + [(v1 + v5) + (v3 + v7)],
+// so both forms give the same bits.
+template <typename R, typename M>
+__device__ __forceinline__ void sample_point_2d_thread(const Geometry &g, const int4 *__restrict__ st_xyz,
+                                                       const R *__restrict__ st_w, const R *__restrict__ nrm, R *acc,
+                                                       int k, M moments) {
+    R p[9], u[3][9];
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+        const long long o = (long long)k * 9 + l;
+        const int4 c = st_xyz[o];
+        R rho, J[3];
+        moments(c.x, c.y, c.z, rho, J);
+        const R wp = st_w[2 * o], wu = st_w[2 * o + 1];
+        p[l] = mul_rn(wp, rho);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a][l] = mul_rn(wu, J[a]);
+    }
+    auto tree = [](const R (&v)[9]) {
+        return add_rn(add_rn(add_rn(add_rn(v[0], v[8]), v[4]), add_rn(v[2], v[6])),
+                      add_rn(add_rn(v[1], v[5]), add_rn(v[3], v[7])));
+    };
+    const R P = tree(p);
+    const R U[3] = {tree(u[0]), tree(u[1]), tree(u[2])};
+    accumulate_point(acc + 5 * (long long)k, P, U, nrm + 4 * (long long)k);
 }
 
 template <typename S, typename M>

@@ -46,8 +46,7 @@ def test_batch_3d_matches_single_and_oracle(wlb):
     for i, p in enumerate(probs):
         with wlb.Solver(p) as s:
             Fs = s.run()
-        ax = p["wave_axis"]
-        assert abs(F[i, ax] - Fs[ax]) <= 1e-6 * abs(Fs[ax]), (i, F[i], Fs)
+        assert np.array_equal(F[i], Fs), (i, F[i], Fs)
     o = oracle.run(probs[0])["force"]
     assert abs(F[0, 2] - o[2]) <= 1e-3 * abs(o[2])
 
@@ -62,12 +61,12 @@ def test_batch_2d_ragged(wlb, precision):
              for (n, lam, R, per) in specs]
     with wlb.Batch(probs) as b:
         F = b.run()
-    # FP16: a one-ulp FP32 difference between kernels can flip one FP16 rounding
-    tol = {"f32": 1e-6, "f64": 1e-12, "f16": 1e-3}[precision]
+    # the batch samples 2D points one thread each, summing the stencil in the
+    # order of the single-lattice warp reduction: the same bits
     for i, p in enumerate(probs):
         with wlb.Solver(p) as s:
             Fs = s.run()
-        assert abs(F[i, 1] - Fs[1]) <= tol * abs(Fs[1]), (i, F[i], Fs)
+        assert np.array_equal(F[i], Fs), (i, F[i], Fs)
 
 
 def test_batch_autotune_and_member_without_window(wlb):
