@@ -37,7 +37,7 @@ namespace {
 constexpr long long kWaitLimit = 1LL << 22;  // mbarrier polls before giving up
 constexpr int kMaxRows = 16;                 // S1 rows (warps) per CTA
 constexpr int kRingPlanes = 3;               // +-y exchange ring
-constexpr int kStages = 2;                   // staged A planes
+constexpr int kStages = 2;                   // staged A planes (three: 5-row slabs on 256^3, slower)
 
 // Threads per CTA: a warp per S1 row; rows with eight values per lane keep
 // enough registers (about 180) with at most eleven warps.
@@ -339,14 +339,12 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
             bulk_load(c2s + ((size_t)buf * rmax + r) * rowel, c2f + row0 * nx, c2_bytes, &bar[buf]);
         }
     };
-    int flag_next = 0;  // warp 0: band flag of plane index k + 2, for the issue in iteration k
+    int flag_next = 0;  // warp 0: band flag of plane index k + kStages, for the issue in iteration k
     if (warp == 0) {
-        const int f0 = band_flag(0), f1 = band_flag(1);
-        flag_next = band_flag(2);
-        issue(0, f0);
-        issue(1, f1);
+        for (int j = 0; j < kStages && j < L; ++j) issue(j, band_flag(j));
+        flag_next = band_flag(kStages);
     }
-    __syncthreads();  // row flags of stages 0 and 1
+    __syncthreads();  // row flags of the first stages
 
     // warp -> S1 row `row` of the slab (y0-1+row) and segment `seg` of it
     // (cells xs .. xs + 32*W*CH - 1)
@@ -452,9 +450,9 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
             failed = 1;
             break;
         }
-        if (warp == 0 && k + 2 < L) {
-            issue(k + 2, flag_next);
-            flag_next = band_flag(k + 3);  // used in the next iteration
+        if (warp == 0 && k + kStages < L) {
+            issue(k + kStages, flag_next);
+            flag_next = band_flag(k + kStages + 1);  // used in the next iteration
         }
         if (k >= 2 && s2_row) {
             const int q = (p + nz - 1) % nz;
@@ -504,8 +502,8 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
     }
     if (failed && threadIdx.x == 0) {
         atomicExch(err, 2);  // reported as WLB_ERR_TIMEOUT
-        // let the copies still in flight (stages k and k+1) land before exit
-        for (int j = k; j < k + 2 && j < L; ++j) bar_wait(&bar[j % kStages], (uint32_t)((j / kStages) & 1));
+        // let the copies still in flight (stages k .. k + kStages - 1) land before exit
+        for (int j = k; j < k + kStages && j < L; ++j) bar_wait(&bar[j % kStages], (uint32_t)((j / kStages) & 1));
     }
 }
 
