@@ -45,6 +45,8 @@ def _dist():
     return rank, world, local
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, NVIDIA's figure (context beside the measured copy peak)
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -317,6 +319,7 @@ def run_gpu(args, prob):
             "force": [float(v) for v in F],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                          "kernel": ("update2_slab, 2 steps/launch, %d-row slabs" % info.two_step_rows
                                     if spl == 2 else "update_rows")
                                    + " (%s storage)" % args.precision, "bytes_per_cell_per_launch": bpu,
