@@ -281,7 +281,9 @@ typedef struct {
     int steps_per_launch;           /* 2: every launch advances all lattices two
                                        steps (wlb_set_two_step's kernel, one
                                        launch over every lattice's slabs)      */
-    int total_ctas;                 /* blocks of that launch, 0 if 1 step     */
+    int total_ctas;                 /* work units of that launch: blocks (3D)
+                                       or warps, one per row chunk (2D); 0 if
+                                       one step per launch                    */
 } wlb_batch_info;
 
 wlb_status wlb_batch_workspace_bytes(const wlb_params *ps, int count, size_t *bytes);
@@ -290,13 +292,15 @@ wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws
 wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tuning *best);
 wlb_status wlb_batch_run(wlb_batch *b, double *forces_out);
 wlb_status wlb_batch_get_info(const wlb_batch *b, wlb_batch_info *out);
-/* Steps two per launch for the whole batch: on by default when every lattice
- * is 3D, periodic, FP32 or FP16 with rows the two-step kernel takes, and all
- * run lengths, windows and periods are even; then one launch of the slab
- * kernel covers every lattice (each with its own slab plan) and a batched
- * sampling launch adds the sums of both steps.  Bit-identical to one step per
- * launch.  enable = 0 returns to one step per launch; enable != 0 where the
- * batch does not qualify gives WLB_ERR_ARG. */
+/* Steps two per launch for the whole batch: on by default when all run
+ * lengths, windows and periods are even and every lattice is periodic and
+ * either 3D with FP32/FP16 rows the two-step slab kernel takes (then one
+ * launch of it covers every lattice, each with its own slab plan) or 2D with
+ * rows of at most 64 sixteen-byte vectors and 8 values per lane (then each
+ * warp sweeps a chunk of 32 rows of one lattice, both steps in registers).
+ * A batched sampling launch adds the sums of both steps.  Bit-identical to
+ * one step per launch.  enable = 0 returns to one step per launch;
+ * enable != 0 where the batch does not qualify gives WLB_ERR_ARG. */
 wlb_status wlb_batch_set_two_step(wlb_batch *b, int enable);
 const char *wlb_batch_last_error(const wlb_batch *b);
 wlb_status wlb_batch_destroy(wlb_batch *b);

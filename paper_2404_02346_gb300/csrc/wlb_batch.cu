@@ -286,7 +286,8 @@ struct wlb_batch {
     // two steps per launch (all lattices 3D periodic FP32/FP16 with even step
     // counts): one launch of the slab kernel over every lattice's CTAs
     bool two_ok = false, two = false, two_full = false;
-    int two_threads = 0, total_ctas = 0;
+    int two_threads = 0, total_ctas = 0;  // 2D: total_ctas counts warps (row chunks)
+    int two_ch = 1;                       // 2D: chunks per lane of the widest row
     size_t two_smem = 0;
     int *d_cta_lat = nullptr, *d_cta_first = nullptr;
     char err[512] = {0};
@@ -364,10 +365,14 @@ cudaError_t issue_steps(wlb_batch *b, int nsteps, int threads, int bps, cudaStre
     if (b->two) {  // step counts are even in this mode
         if (nsteps % 2) return cudaErrorInvalidValue;
         for (int k = 0; k < nsteps; k += 2) {
-            cudaError_t e = wlb::launch_batch_two_steps(b->prec, b->two_full, b->d_lats, b->d_cta_lat,
-                                                        b->d_cta_first, b->total_ctas, b->two_threads, b->two_smem,
-                                                        b->d_pt_lat, b->d_pt_begin, b->total_points, b->d_step,
-                                                        b->d_done, grid, s);
+            cudaError_t e =
+                b->dim == 3
+                    ? wlb::launch_batch_two_steps(b->prec, b->two_full, b->d_lats, b->d_cta_lat, b->d_cta_first,
+                                                  b->total_ctas, b->two_threads, b->two_smem, b->d_pt_lat,
+                                                  b->d_pt_begin, b->total_points, b->d_step, b->d_done, grid, s)
+                    : wlb::launch_batch2d_two_steps(b->prec, b->two_ch, b->d_lats, b->d_cta_lat, b->d_cta_first,
+                                                    b->total_ctas, b->d_pt_lat, b->d_pt_begin, b->total_points,
+                                                    b->d_step, b->d_done, grid, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -602,10 +607,16 @@ wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws
             e = cudaMemcpy(b->d_class_row_lat[k], rl.data(), sizeof(int) * rl.size(), cudaMemcpyHostToDevice);
     }
     // two steps per launch where every lattice takes it (plans land in b->lat)
-    bool even = b->dim == 3;
+    bool even = true;
     for (int i = 0; i < count && even; ++i)
         even = b->lat[i].n_steps % 2 == 0 && b->lat[i].window_begin % 2 == 0 && b->lat[i].period % 2 == 0;
-    if (even && wlb::plan_batch_two_steps(b->prec, b->lat.data(), count, &b->two_threads, &b->two_smem, &b->two_full)) {
+    int tasks2d = 0;
+    const bool planned =
+        even && (b->dim == 3 ? wlb::plan_batch_two_steps(b->prec, b->lat.data(), count, &b->two_threads,
+                                                         &b->two_smem, &b->two_full)
+                             : wlb::plan_batch2d_two_steps(b->prec, b->lat.data(), count, &tasks2d, &b->two_ch));
+    if (planned && b->dim == 2) b->two_threads = b->lat[0].plan.threads;  // warps of a block
+    if (planned) {
         std::vector<int> first(count + 1, 0), owner;
         for (int i = 0; i < count; ++i) {
             const int n = b->lat[i].plan.nslab * b->lat[i].plan.chunks;

@@ -248,25 +248,36 @@ template <typename R, typename M>
 __device__ __forceinline__ void sample_point_2d_thread(const Geometry &g, const int4 *__restrict__ st_xyz,
                                                        const R *__restrict__ st_w, const R *__restrict__ nrm, R *acc,
                                                        int k, M moments) {
-    R p[9], u[3][9];
-#pragma unroll
-    for (int l = 0; l < 9; ++l) {
+    struct T {
+        R p, u[3];
+    };
+    auto term = [&](int l) {  // stencil cell l: (delta c^2 rho1, delta J1 / rho0)
         const long long o = (long long)k * 9 + l;
         const int4 c = st_xyz[o];
         R rho, J[3];
         moments(c.x, c.y, c.z, rho, J);
         const R wp = st_w[2 * o], wu = st_w[2 * o + 1];
-        p[l] = mul_rn(wp, rho);
+        T v;
+        v.p = mul_rn(wp, rho);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) u[a][l] = mul_rn(wu, J[a]);
-    }
-    auto tree = [](const R (&v)[9]) {
-        return add_rn(add_rn(add_rn(add_rn(v[0], v[8]), v[4]), add_rn(v[2], v[6])),
-                      add_rn(add_rn(v[1], v[5]), add_rn(v[3], v[7])));
+        for (int a = 0; a < 3; ++a) v.u[a] = mul_rn(wu, J[a]);
+        return v;
     };
-    const R P = tree(p);
-    const R U[3] = {tree(u[0]), tree(u[1]), tree(u[2])};
-    accumulate_point(acc + 5 * (long long)k, P, U, nrm + 4 * (long long)k);
+    auto add = [](const T &x, const T &y) {
+        T v;
+        v.p = add_rn(x.p, y.p);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v.u[a] = add_rn(x.u[a], y.u[a]);
+        return v;
+    };
+    // evaluated in tree order, so that few partial sums are live at a time
+    T s = add(term(0), term(8));
+    s = add(s, term(4));
+    s = add(s, add(term(2), term(6)));
+    T r = add(term(1), term(5));
+    r = add(r, add(term(3), term(7)));
+    s = add(s, r);
+    accumulate_point(acc + 5 * (long long)k, s.p, s.u, nrm + 4 * (long long)k);
 }
 
 template <typename S, typename M>

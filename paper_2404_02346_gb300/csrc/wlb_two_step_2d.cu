@@ -1,0 +1,361 @@
+// Two lattice steps per launch for batches of 2D lattices (D2Q5, periodic).
+//
+// The update is the fused advection + tau = 1/2 collision (Sec. V, Eqs.
+// 62-64, 71) applied twice: S1 takes state t (buffer A) to t+1, S2 takes t+1
+// to t+2 (buffer B).  In 2D a lattice row needs no neighbour row of the same
+// time level besides those above and below it, so each warp sweeps a chunk of
+// rows ya .. yb-1 on its own: for p = ya-1 .. yb it computes S1 on row p from
+// A (rows p-1, p, p+1, read directly, one row ahead), then S2 on row p-1 from
+// its registers:
+//   rest, +x, -x   from S1 of row p-1 (x shift by shuffles, periodic wrap),
+//   +y             from S1 of row p-2,
+//   -y             from S1 of row p.
+// No shared memory, no barrier, no warp waits for another; the rows just
+// outside a chunk are computed by both warps that need them.  The t+1 values
+// are rounded to the storage type as a stored state would be, so results are
+// bit-identical to two single steps.
+#include "wlb_handle.cuh"
+#include "wlb_kernels.cuh"
+
+namespace wlb {
+namespace {
+
+constexpr int kRowsPerWarp = 32;   // row chunk of one warp (two halo rows per chunk)
+constexpr int kWarpsPerBlock = 2;  // small blocks: as many warps per SM as registers allow
+
+// The value a stored state holds for v (storage rounding).
+template <typename S> __device__ __forceinline__ typename Store<S>::R as_stored(typename Store<S>::R v) { return v; }
+template <> __device__ __forceinline__ float as_stored<__half>(float v) { return __half2float(__float2half_rn(v)); }
+
+// +x / -x pulls of a row held as CH chunks of W values per lane in slots
+// j = c * 32 + lane (x = j * W + e), the first V slots being cells: the value
+// from x - 1 and from x + 1, periodic in x.
+template <typename R, int CH, int W>
+__device__ __forceinline__ void row_shift(const R (&px)[CH][W], const R (&mx)[CH][W], int lane, int V,
+                                          R (&fpx)[CH][W], R (&fmx)[CH][W]) {
+    R up[CH], dn[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        up[c] = __shfl_sync(kFull, px[c][W - 1], (lane + 31) & 31);
+        dn[c] = __shfl_sync(kFull, mx[c][0], (lane + 1) & 31);
+    }
+    // wrap: +x at x = 0 is the last cell's value, -x at the last cell is x = 0's
+    R lastv = px[0][W - 1];
+#pragma unroll
+    for (int c = 1; c < CH; ++c)
+        if (c == (V - 1) >> 5) lastv = px[c][W - 1];
+    const R left = __shfl_sync(kFull, lastv, (V - 1) & 31);
+    const R right = __shfl_sync(kFull, mx[0][0], 0);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        fpx[c][0] = lane == 0 ? (c == 0 ? left : up[c - 1]) : up[c];
+#pragma unroll
+        for (int e = 1; e < W; ++e) fpx[c][e] = px[c][e - 1];
+#pragma unroll
+        for (int e = 0; e < W - 1; ++e) fmx[c][e] = mx[c][e + 1];
+        const R next = lane == 31 ? (c == CH - 1 ? right : dn[c + 1]) : dn[c];
+        fmx[c][W - 1] = c * 32 + lane == V - 1 ? right : next;
+    }
+}
+
+// The sweep of one row chunk of one lattice by one warp (warp-uniform flow).
+template <typename S, int CH>
+__device__ __forceinline__ void sweep_rows(const BatchLat &L, int chunk, long long t, int lane) {
+    using R = typename Store<S>::R;
+    constexpr int W = Store<S>::W;
+    const int nx = L.g.n[0], ny = L.g.n[1];
+    const long long nc = L.g.ncell;
+    const int V = nx / W, yc = L.plan.zc;
+    const int ya = chunk * yc, yb = min(ny, ya + yc);
+    const int src = (int)((t >> 1) & 1);
+    const S *__restrict__ A = (const S *)L.b.pop[src];
+    S *__restrict__ B = (S *)L.b.pop[src ^ 1];
+    const uint8_t *__restrict__ cls = L.b.cls;
+    const R *__restrict__ c2f = (const R *)L.b.c2;
+    const R c0sq = (R)(L.g.c0 * L.g.c0), cpsq = (R)(L.g.cp * L.g.cp);
+    bool act[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) act[c] = c * 32 + lane < V;
+    R n0[CH][W], n1[CH][W], n2[CH][W], cq[CH][W];  // S1 of row p-1: rest, +x, -x; its c^2
+    R py0[CH][W], py1[CH][W];                      // +y of S1 rows p-2, p-1
+    // the values S1 of row p pulls and its class bytes, loaded one row ahead
+    R f[5][CH][W];
+    unsigned long long cl[CH];
+    auto load_row = [&](int p, R (&g)[5][CH][W], unsigned long long (&gc)[CH]) {
+        const int y = (p + ny) % ny, ym = (y + ny - 1) % ny, yp = (y + 1) % ny;
+        const long long r0 = (long long)y * nx;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int x0 = (c * 32 + lane) * W;
+            if (act[c]) {
+                Store<S>::load(A + r0 + x0, g[0][c]);
+                Store<S>::load(A + nc + r0 + x0, g[1][c]);
+                Store<S>::load(A + 2 * nc + r0 + x0, g[2][c]);
+                Store<S>::load(A + 3 * nc + (long long)ym * nx + x0, g[3][c]);
+                Store<S>::load(A + 4 * nc + (long long)yp * nx + x0, g[4][c]);
+                gc[c] = load_classes<W>(cls + r0 + x0);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 5; ++i)
+#pragma unroll
+                    for (int e = 0; e < W; ++e) g[i][c][e] = R(0);
+                gc[c] = 0;
+            }
+        }
+    };
+    load_row(ya - 1, f, cl);
+    for (int k = 0, p = ya - 1; p <= yb; ++k, ++p) {
+        const int y = (p + ny) % ny;
+        const long long r0 = (long long)y * nx;
+        R fn[5][CH][W];
+        unsigned long long cln[CH];
+        if (p < yb) load_row(p + 1, fn, cln);
+        R cs[CH][W];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int x0 = (c * 32 + lane) * W;
+#pragma unroll
+            for (int e = 0; e < W; ++e) {  // the c^2 of the one-step kernels
+                const unsigned kc = (unsigned)(cl[c] >> (8 * e)) & 0xffu;
+                cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : c2f[r0 + x0 + e]);
+            }
+        }
+        R fpx[CH][W], fmx[CH][W];
+        row_shift<R, CH, W>(f[1], f[2], lane, V, fpx, fmx);
+        R o[5][CH][W];  // S1 of row p in storage precision
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const R fin[5] = {f[0][c][e], fpx[c][e], fmx[c][e], f[3][c][e], f[4][c][e]};
+                R t5[5];
+                collide_half<R, 2>(cs[c][e], fin, t5);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) o[i][c][e] = as_stored<S>(t5[i]);
+            }
+        if (k >= 2) {  // S2 on row q = p - 1
+            const int q = (y + ny - 1) % ny;
+            const long long rq = (long long)q * nx;
+            R gpx[CH][W], gmx[CH][W];
+            row_shift<R, CH, W>(n1, n2, lane, V, gpx, gmx);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                if (!act[c]) continue;
+                const int x0 = (c * 32 + lane) * W;
+                R out[5][W];
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    const R fin[5] = {n0[c][e], gpx[c][e], gmx[c][e], py0[c][e], o[4][c][e]};
+                    R t5[5];
+                    collide_half<R, 2>(cq[c][e], fin, t5);
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) out[i][e] = t5[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 5; ++i) Store<S>::store(B + i * nc + rq + x0, out[i]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                py0[c][e] = py1[c][e];
+                py1[c][e] = o[3][c][e];
+                n0[c][e] = o[0][c][e];
+                n1[c][e] = o[1][c][e];
+                n2[c][e] = o[2][c][e];
+                cq[c][e] = cs[c][e];
+            }
+        if (p < yb) {
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                cl[c] = cln[c];
+#pragma unroll
+                for (int i = 0; i < 5; ++i)
+#pragma unroll
+                    for (int e = 0; e < W; ++e) f[i][c][e] = fn[i][c][e];
+            }
+        }
+    }
+}
+
+// One launch: warp w sweeps chunk w - task_first[i] of lattice i = task_lat[w]
+// (lattices past their n_steps skip).  The state at step t is in buffer
+// (t / 2) & 1; the last block to finish advances the step by two (every block
+// has read it by then).
+template <typename S, int CH>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) batch2d_update2(const BatchLat *__restrict__ lats,
+                                                                       const int *__restrict__ task_lat,
+                                                                       const int *__restrict__ task_first,
+                                                                       int total_tasks, long long *step,
+                                                                       unsigned *done) {
+    const long long t = *step;
+    const int lane = threadIdx.x & 31;
+    const int task = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (task < total_tasks) {
+        const int i = task_lat[task];
+        const BatchLat &L = lats[i];
+        if (t < L.n_steps) sweep_rows<S, CH>(L, task - task_first[i], t, lane);  // warp-uniform
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(done, 1u);
+        if (ticket == gridDim.x - 1) {
+            *done = 0;
+            *step = t + 2;
+            __threadfence();
+        }
+    }
+}
+
+// rho1 and J1 of cell (x, y) at t+1 from the populations A of time t: each of
+// the five values the cell pulls is the t+1 value of the neighbour it comes
+// from, recomputed from A with the update's arithmetic and storage rounding,
+// then summed in the order of pulled_moments.
+template <typename S>
+__device__ __forceinline__ void moments_next_2d(const Geometry &g, const S *__restrict__ A,
+                                                const typename Store<S>::R *__restrict__ c2f, int x, int y,
+                                                typename Store<S>::R &rho, typename Store<S>::R (&J)[3]) {
+    using R = typename Store<S>::R;
+    const int nx = g.n[0], ny = g.n[1];
+    const long long nc = g.ncell;
+    auto dn = [](int v, int n) { return v == 0 ? n - 1 : v - 1; };
+    auto up = [](int v, int n) { return v == n - 1 ? 0 : v + 1; };
+    auto post = [&](int i, int cx, int cy) -> R {  // f*_i(cx, cy) at t+1
+        const long long row = (long long)cy * nx;
+        const R fin[5] = {Store<S>::get(A + row + cx), Store<S>::get(A + nc + row + dn(cx, nx)),
+                          Store<S>::get(A + 2 * nc + row + up(cx, nx)),
+                          Store<S>::get(A + 3 * nc + (long long)dn(cy, ny) * nx + cx),
+                          Store<S>::get(A + 4 * nc + (long long)up(cy, ny) * nx + cx)};
+        R o[5];
+        collide_half<R, 2>(c2f[row + cx], fin, o);
+        return as_stored<S>(o[i]);
+    };
+    const R f0 = post(0, x, y);
+    const R fpx = post(1, dn(x, nx), y);
+    const R fmx = post(2, up(x, nx), y);
+    const R fpy = post(3, x, dn(y, ny));
+    const R fmy = post(4, x, up(y, ny));
+    rho = f0 + fpx + fmx + fpy + fmy;
+    J[0] = fpx - fmx;
+    J[1] = fpy - fmy;
+    J[2] = R(0);
+}
+
+// Sampling of both steps of a launch, one thread per point: sums of t (the
+// stored state) and t+1 (recomputed) in that order, then the period fold when
+// t+1 closes a period (periods and windows are even).
+template <typename S>
+__global__ void __launch_bounds__(256) batch2d_sample_two(const BatchLat *__restrict__ lats,
+                                                          const int *__restrict__ pt_lat,
+                                                          const long long *__restrict__ pt_begin,
+                                                          long long total_points, const long long *step) {
+    using R = typename Store<S>::R;
+    const long long t = *step;
+    const long long threads = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < total_points; p += threads) {
+        const int i = pt_lat[p];
+        const BatchLat &L = lats[i];
+        if (t < L.window_begin || t >= L.n_steps) continue;
+        const int k = (int)(p - pt_begin[i]);
+        const S *A = (const S *)L.b.pop[(t >> 1) & 1];
+        const R *st_w = (const R *)L.b.st_w, *nrm = (const R *)L.b.nrm;
+        R *acc = (R *)L.b.acc;
+        sample_point_2d_thread(L.g, L.b.st_xyz, st_w, nrm, acc, k, [&](int x, int y, int z, R &rho, R(&J)[3]) {
+            pulled_moments(L.g, A, x, y, z, rho, J);
+        });
+        sample_point_2d_thread(L.g, L.b.st_xyz, st_w, nrm, acc, k, [&](int x, int y, int, R &rho, R(&J)[3]) {
+            moments_next_2d(L.g, A, (const R *)L.b.c2, x, y, rho, J);
+        });
+        if ((t + 2 - L.window_begin) % L.period == 0) {
+            const double scale = 1.0 / (L.g.pop_scale * L.g.pop_scale);
+            R *a = acc + 5 * (long long)k;
+            double *a64 = L.b.acc64 + 5 * (long long)k;
+            bool bad = false;
+            for (int j = 0; j < 5; ++j) {
+                const double v = fold_value(a64[j], (double)a[j], scale);
+                a64[j] = v;
+                a[j] = R(0);
+                bad |= !isfinite(v);
+            }
+            if (bad) atomicExch(L.b.err, 1);
+        }
+    }
+}
+
+template <typename S>
+bool plan_for(BatchLat *lats, int count, int *tasks, int *chunks_per_lane) {
+    constexpr int W = Store<S>::W;
+    int ch = 1, total = 0;
+    for (int i = 0; i < count; ++i) {
+        const Geometry &g = lats[i].g;
+        if (g.dim != 2 || g.driven || g.n[0] % W) return false;
+        const int V = g.n[0] / W;
+        const int c = (V + 31) / 32;
+        if (c > 2 || W * c > 8) return false;  // at most 8 values per lane
+        ch = c > ch ? c : ch;
+        TwoStepPlan pl;
+        pl.zc = g.n[1] < kRowsPerWarp ? g.n[1] : kRowsPerWarp;
+        pl.chunks = (g.n[1] + pl.zc - 1) / pl.zc;
+        pl.nslab = 1;
+        pl.nseg = 1;
+        pl.H = 1;
+        pl.chunks_per_lane = c;
+        pl.threads = 32 * kWarpsPerBlock;
+        lats[i].plan = pl;
+        total += pl.chunks;
+    }
+    *tasks = total;
+    *chunks_per_lane = ch;
+    return true;
+}
+
+template <typename S>
+cudaError_t launch_for(int ch, const BatchLat *lats, const int *task_lat, const int *task_first, int total_tasks,
+                       const int *pt_lat, const long long *pt_begin, long long total_points, long long *step,
+                       unsigned *done, int sample_grid, cudaStream_t s) {
+    if (total_points > 0) {
+        const long long need = (total_points + 255) / 256;
+        const int g = (int)(need < sample_grid ? need : sample_grid);
+        batch2d_sample_two<S><<<g, 256, 0, s>>>(lats, pt_lat, pt_begin, total_points, step);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int blocks = (total_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int threads = 32 * kWarpsPerBlock;
+    if (ch == 1) batch2d_update2<S, 1><<<blocks, threads, 0, s>>>(lats, task_lat, task_first, total_tasks, step, done);
+    else if constexpr (Store<S>::W * 2 <= 8)
+        batch2d_update2<S, 2><<<blocks, threads, 0, s>>>(lats, task_lat, task_first, total_tasks, step, done);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool plan_batch2d_two_steps(Prec p, BatchLat *lats, int count, int *tasks, int *chunks_per_lane) {
+    switch (p) {
+        case Prec::F16: return plan_for<__half>(lats, count, tasks, chunks_per_lane);
+        case Prec::F64: return plan_for<double>(lats, count, tasks, chunks_per_lane);
+        default: return plan_for<float>(lats, count, tasks, chunks_per_lane);
+    }
+}
+
+cudaError_t launch_batch2d_two_steps(Prec p, int chunks_per_lane, const BatchLat *lats, const int *task_lat,
+                                     const int *task_first, int total_tasks, const int *pt_lat,
+                                     const long long *pt_begin, long long total_points, long long *step,
+                                     unsigned *done, int sample_grid, cudaStream_t s) {
+    switch (p) {
+        case Prec::F16:
+            return launch_for<__half>(chunks_per_lane, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
+                                      total_points, step, done, sample_grid, s);
+        case Prec::F64:
+            return launch_for<double>(chunks_per_lane, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
+                                      total_points, step, done, sample_grid, s);
+        default:
+            return launch_for<float>(chunks_per_lane, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
+                                     total_points, step, done, sample_grid, s);
+    }
+}
+
+}  // namespace wlb

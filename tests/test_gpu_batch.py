@@ -60,7 +60,14 @@ def test_batch_2d_ragged(wlb, precision):
                                n_periods=per, n_avg_periods=2, precision=precision)
              for (n, lam, R, per) in specs]
     with wlb.Batch(probs) as b:
+        # even lengths and rows of at most 64 vectors: two steps per launch,
+        # except FP64, whose 192-cell rows need three chunks per lane
+        two = b.info().steps_per_launch == 2
+        assert two == (precision != "f64")
         F = b.run()
+        if two:
+            b.set_two_step(False)
+            assert np.array_equal(b.run(), F)
     # the batch samples 2D points one thread each, summing the stencil in the
     # order of the single-lattice warp reduction: the same bits
     for i, p in enumerate(probs):
