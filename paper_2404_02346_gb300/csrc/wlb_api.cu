@@ -293,7 +293,7 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
         wlb_destroy(h);
         return WLB_ERR_CUDA;
     }
-    // unsampled steps two per launch wherever the kernel applies (bit-identical)
+    // steps two per launch wherever the kernel applies (bit-identical)
     if (wlb::two_step_supported(h->g, h->prec) && wlb::plan_two_steps(h->g, h->prec, 0, 1, &h->two_plan) == cudaSuccess)
         h->two_step = true;
     cudaGetLastError();
@@ -384,7 +384,7 @@ wlb_status wlb_force(wlb_handle *h, double force_out[3]) {
     int flag;
     memcpy(&flag, h->host_out + 4, sizeof(int));
     for (int i = 0; i < 3; ++i) force_out[i] = h->host_out[i];
-    if (flag == 2) return fail(h, WLB_ERR_TIMEOUT, "double-step plane wait limit reached");
+    if (flag == 2) return fail(h, WLB_ERR_TIMEOUT, "two-step staging wait limit reached");
     if (flag) return fail(h, WLB_ERR_UNSTABLE, "non-finite accumulators");
     return WLB_OK;
 }

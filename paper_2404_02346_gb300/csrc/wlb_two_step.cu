@@ -1,5 +1,6 @@
-// Two lattice steps per launch (3D, periodic, unsampled steps): temporal
-// blocking in y-slabs with recomputed halo rows.
+// Two lattice steps per launch (3D, periodic): temporal blocking in y-slabs
+// with recomputed halo rows; in sampled steps a sampling kernel beside it adds
+// the surface sums of both steps.
 //
 // The update is the fused advection + tau = 1/2 collision of update_rows
 // (Sec. V, Eqs. 62-64, 71) applied twice: S1 takes state t (buffer A) to t+1,
@@ -19,10 +20,10 @@
 // their class bytes and, for rows holding interface-band cells (a per-row
 // flag from setup, read one plane ahead), their c^2 rows are staged in shared
 // memory by 1-D bulk (TMA) copies issued two planes ahead and completing on an
-// mbarrier (two stages), so no warp waits on a global load of its own.  No CTA waits for another
-// CTA: one launch reads A and writes B once, about half the HBM traffic of two
-// single steps, plus the halo rows, which neighbouring slabs read at the same
-// time (L2 hits).  Results are bit-identical to two single steps: the same
+// mbarrier (two stages), so no warp waits on a global load of its own.  No CTA
+// waits for another CTA: one launch reads A and writes B once, about half the
+// HBM traffic of two single steps, plus the halo rows, which neighbouring
+// slabs read at the same time (L2 hits).  Results are bit-identical to two single steps: the same
 // per-cell arithmetic, and the t+1 values are rounded to the storage type as
 // a single step would store them.
 #include <algorithm>
