@@ -41,10 +41,10 @@ constexpr int kRingPlanes = 3;               // +-y exchange ring
 constexpr int kStages = 2;                   // staged A planes (three: 5-row slabs on 256^3, slower)
 
 // Threads per CTA: a warp per S1 row; rows with eight values per lane keep
-// enough registers (about 180) with at most eleven warps.
+// enough registers (about 165) with at most twelve warps.
 template <typename S, int CH>
 constexpr int two_step_threads() {
-    return Store<S>::W * CH <= 4 ? 32 * kMaxRows : 32 * 11;
+    return Store<S>::W * CH <= 4 ? 32 * kMaxRows : 32 * 12;
 }
 
 // Shared memory per S1 row: two staged planes of seven populations (storage
@@ -623,11 +623,10 @@ int chunks_for(int V, int mode) {
 }
 
 // Slab height H (rows <= smem and thread limits; `want` > 0 asks for one)
-// and the z-chunk count minimising the estimated time: waves x planes per CTA
-// x rows moved per plane (H + 2 read, H written), one CTA per SM.  Among
-// heights within 5 % of the best estimate the tallest is taken: each plane
-// costs a CTA a fixed latency besides its bytes, so fewer, taller slabs win
-// where the bytes alone do not decide.
+// and the z-chunk count minimising the estimated time, one CTA per SM: for
+// FP32 waves x planes per CTA x rows moved per plane (H + 2 read, H written);
+// for FP16 storage, whose planes cost a CTA mostly a fixed latency, waves x
+// planes.  Among heights within 5 % of the best estimate the tallest is taken.
 template <typename S, int CH>
 cudaError_t plan_ch(const Geometry &g, int want, int nseg, TwoStepPlan *pl) {
     int dev = 0, sms = 0, smem_max = 0;
@@ -654,7 +653,9 @@ cudaError_t plan_ch(const Geometry &g, int want, int nseg, TwoStepPlan *pl) {
             const int zc = (nz + C - 1) / C;
             const int used = (nz + zc - 1) / zc;
             const long long waves = ((long long)nslab * used + sms - 1) / sms;
-            const long long cost = waves * (zc + 2) * (2LL * H + 2);
+            // FP32: time follows the rows moved per plane; FP16 storage halves
+            // the bytes and a plane's fixed latency dominates: count planes
+            const long long cost = sizeof(S) == 2 ? waves * (zc + 2) : waves * (zc + 2) * (2LL * H + 2);
             if (cost_h[H] < 0 || cost < cost_h[H]) {
                 cost_h[H] = cost;
                 per_h[H].H = H;
