@@ -8,6 +8,7 @@
 // by the last block of each update launch, so a chunk of steps is one CUDA
 // graph replayed without host work.  Lattices with fewer steps than the longest
 // one stop at their own n_steps (their rows are skipped).
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -285,10 +286,11 @@ struct wlb_batch {
     int graph_threads = 0, graph_bps = 0, graph_two = -1;
     // two steps per launch (all lattices 3D periodic FP32/FP16 with even step
     // counts): one launch of the slab kernel over every lattice's CTAs
-    bool two_ok = false, two = false, two_full = false;
+    bool two_ok = false, two = false;
     int two_threads = 0, total_ctas = 0;  // 2D: total_ctas counts warps (row chunks)
+    wlb::BatchTwoGroup groups[2];         // 3D: lane-layout groups, one launch each
+    int ngroups = 0;
     int two_ch = 1;                       // 2D: chunks per lane of the widest row
-    size_t two_smem = 0;
     int *d_cta_lat = nullptr, *d_cta_first = nullptr;
     char err[512] = {0};
 };
@@ -367,9 +369,9 @@ cudaError_t issue_steps(wlb_batch *b, int nsteps, int threads, int bps, cudaStre
         for (int k = 0; k < nsteps; k += 2) {
             cudaError_t e =
                 b->dim == 3
-                    ? wlb::launch_batch_two_steps(b->prec, b->two_full, b->d_lats, b->d_cta_lat, b->d_cta_first,
-                                                  b->total_ctas, b->two_threads, b->two_smem, b->d_pt_lat,
-                                                  b->d_pt_begin, b->total_points, b->d_step, b->d_done, grid, s)
+                    ? wlb::launch_batch_two_steps(b->prec, b->groups, b->ngroups, b->d_lats, b->d_cta_lat,
+                                                  b->d_cta_first, b->d_pt_lat, b->d_pt_begin, b->total_points,
+                                                  b->d_step, b->d_done, grid, s)
                     : wlb::launch_batch2d_two_steps(b->prec, b->two_ch, b->d_lats, b->d_cta_lat, b->d_cta_first,
                                                     b->total_ctas, b->d_pt_lat, b->d_pt_begin, b->total_points,
                                                     b->d_step, b->d_done, grid, s);
@@ -612,18 +614,30 @@ wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws
         even = b->lat[i].n_steps % 2 == 0 && b->lat[i].window_begin % 2 == 0 && b->lat[i].period % 2 == 0;
     int tasks2d = 0;
     const bool planned =
-        even && (b->dim == 3 ? wlb::plan_batch_two_steps(b->prec, b->lat.data(), count, &b->two_threads,
-                                                         &b->two_smem, &b->two_full)
+        even && (b->dim == 3 ? wlb::plan_batch_two_steps(b->prec, b->lat.data(), count, b->groups, &b->ngroups)
                              : wlb::plan_batch2d_two_steps(b->prec, b->lat.data(), count, &tasks2d, &b->two_ch));
-    if (planned && b->dim == 2) b->two_threads = b->lat[0].plan.threads;  // warps of a block
     if (planned) {
+        // CTA (3D) or warp (2D) -> lattice table, the lattices of each 3D
+        // lane-layout group together; first[i] = lattice i's first entry
         std::vector<int> first(count + 1, 0), owner;
-        for (int i = 0; i < count; ++i) {
-            const int n = b->lat[i].plan.nslab * b->lat[i].plan.chunks;
-            first[i + 1] = first[i] + n;
-            owner.insert(owner.end(), (size_t)n, i);
+        const int ngr = b->dim == 3 ? b->ngroups : 1;
+        for (int k = 0; k < ngr; ++k) {
+            const int begin = (int)owner.size();
+            for (int i = 0; i < count; ++i) {
+                if (b->dim == 3 && b->lat[i].plan.chunks_per_lane != b->groups[k].ch) continue;
+                const int n = b->lat[i].plan.nslab * b->lat[i].plan.chunks;
+                first[i] = (int)owner.size();
+                owner.insert(owner.end(), (size_t)n, i);
+            }
+            if (b->dim == 3) {
+                b->groups[k].cta_begin = begin;
+                b->groups[k].ctas = (int)owner.size() - begin;
+                b->two_threads = std::max(b->two_threads, b->groups[k].threads);
+            }
         }
-        b->total_ctas = first[count];
+        if (b->dim == 2) b->two_threads = b->lat[0].plan.threads;  // warps of a block
+        first[count] = (int)owner.size();
+        b->total_ctas = (int)owner.size();
         if (e == cudaSuccess)
             e = cudaMemcpy(b->d_cta_lat, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)

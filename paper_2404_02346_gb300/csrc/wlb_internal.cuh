@@ -107,16 +107,25 @@ struct BatchLat {
     TwoStepPlan plan;
 };
 
-// Batched two steps per launch: plan every lattice (one 16-byte chunk per
-// lane), returning the launch's block size and shared memory and whether all
-// rows are full warps; false if some lattice cannot take it.
-bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, int *threads, size_t *smem, bool *full);
-// One launch of two steps for every active lattice: CTA j works on lattice
-// cta_lat[j] (its CTA j - cta_first[lattice]); with points, a sampling launch
-// before it adds the sums of both steps.  The state at step t is in buffer
-// (t / 2) & 1; the last CTA advances *step by 2.
-cudaError_t launch_batch_two_steps(Prec p, bool full, const BatchLat *lats, const int *cta_lat, const int *cta_first,
-                                   int total_ctas, int threads, size_t smem, const int *pt_lat,
+// Batched two steps per launch (3D): lattices are grouped by lane layout
+// (chunks per lane), one launch of the slab kernel per group.
+struct BatchTwoGroup {
+    int ch = 1;              // 16-byte chunks per lane
+    bool full = false;       // every row of the group made of full warps
+    int threads = 0;         // block size of the group's launch
+    size_t smem = 0;         // its dynamic shared memory
+    int cta_begin = 0, ctas = 0;  // its range of the CTA -> lattice table
+};
+// Plans every lattice (its plan lands in lats[i].plan) and fills up to two
+// groups (cta_begin / ctas are left to the caller); false if some lattice
+// cannot take two steps per launch.
+bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, BatchTwoGroup *groups, int *ngroups);
+// One launch of two steps for every active lattice: CTA j of the table works
+// on lattice cta_lat[j] (its CTA j - cta_first[lattice]); with points, a
+// sampling launch before it adds the sums of both steps.  The state at step t
+// is in buffer (t / 2) & 1; the last group's launch advances *step by 2.
+cudaError_t launch_batch_two_steps(Prec p, const BatchTwoGroup *groups, int ngroups, const BatchLat *lats,
+                                   const int *cta_lat, const int *cta_first, const int *pt_lat,
                                    const long long *pt_begin, long long total_points, long long *step,
                                    unsigned *done, int sample_grid, cudaStream_t s);
 

@@ -28,6 +28,7 @@
 // a single step would store them.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "wlb_handle.cuh"
 #include "wlb_kernels.cuh"
@@ -516,17 +517,19 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1) update2_slab(Sla
 
 // Batched ensembles: CTA j sweeps CTA j - cta_first[i] of lattice
 // i = cta_lat[j] (each lattice with its own plan), skipping lattices past
-// their n_steps.  Every launch is two steps, so the state at step t is in
-// buffer (t / 2) & 1.  The last CTA to finish advances the step: every CTA
-// has read it by then.
+// their n_steps; j = cta_base + blockIdx.x (one launch per lane-layout group).
+// Every launch is two steps, so the state at step t is in buffer (t / 2) & 1.
+// In the last group's launch (advance) the last CTA to finish advances the
+// step: every CTA of every group has read it by then.
 template <typename S, int CH, bool FULL>
 __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
     batch_update2(const BatchLat *__restrict__ lats, const int *__restrict__ cta_lat,
-                  const int *__restrict__ cta_first, long long *step, unsigned *done) {
+                  const int *__restrict__ cta_first, int cta_base, int advance, long long *step, unsigned *done) {
     using R = typename Store<S>::R;
     extern __shared__ __align__(128) unsigned char smem[];
     const long long t = *step;
-    const int i = cta_lat[blockIdx.x];
+    const int j = cta_base + (int)blockIdx.x;
+    const int i = cta_lat[j];
     const BatchLat &L = lats[i];
     if (t < L.n_steps) {  // block-uniform
         const int src = (int)((t >> 1) & 1);
@@ -547,8 +550,9 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
         P.zc = L.plan.zc;
         P.nseg = L.plan.nseg;
         P.err = L.b.err;
-        slab_body<S, CH, FULL>(P, blockIdx.x - cta_first[i], smem);
+        slab_body<S, CH, FULL>(P, j - cta_first[i], smem);
     }
+    if (!advance) return;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -790,26 +794,24 @@ cudaError_t launch_two_steps(const Geometry &g, const Buffers &b, Prec p, const 
 
 namespace {
 
-template <typename S>
-bool plan_batch_for(BatchLat *lats, int count, int *threads, size_t *smem, bool *full) {
+// Each lattice's lane layout: one 16-byte chunk per lane for rows of up to
+// 32 vectors, two (FP32) for wider rows, so that a row of up to 64 vectors is
+// one warp and the slab can be taller; lattices are grouped by it.
+template <typename S, int CH>
+bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, BatchTwoGroup *grp) {
     using R = typename Store<S>::R;
-    int dev = 0, smem_max = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-        return false;
     const size_t fixed = kStages * sizeof(uint64_t) + kStages * (size_t)kMaxRows + 16;
     int t_max = 0;
     size_t s_max = 0;
     bool all_full = true;
-    for (int i = 0; i < count; ++i) {
+    for (int i : members) {
         const Geometry &g = lats[i].g;
         const int V = row_vectors<S>(g);
-        if (g.dim != 3 || g.driven || !V) return false;
-        const int nseg = (V + 31) / 32;
+        const int nseg = (V + 32 * CH - 1) / (32 * CH);
         const size_t per_row = smem_per_row((size_t)g.n[0] * sizeof(S), (size_t)g.n[0] * sizeof(R), (size_t)g.n[0]) +
                                (size_t)kRingPlanes * nseg * 2 * sizeof(R);
         int rows = (int)(((size_t)smem_max - fixed) / per_row);
-        rows = std::min(rows, two_step_threads<S, 1>() / (32 * nseg));
+        rows = std::min(rows, two_step_threads<S, CH>() / (32 * nseg));
         if (rows < 3) return false;
         TwoStepPlan pl;
         pl.H = std::min(rows - 2, g.n[1]);
@@ -819,30 +821,59 @@ bool plan_batch_for(BatchLat *lats, int count, int *threads, size_t *smem, bool 
         pl.zc = (g.n[2] + pl.chunks - 1) / pl.chunks;
         pl.chunks = (g.n[2] + pl.zc - 1) / pl.zc;
         pl.nseg = nseg;
-        pl.chunks_per_lane = 1;
+        pl.chunks_per_lane = CH;
         pl.threads = 32 * nseg * (pl.H + 2);
         pl.smem = per_row * (pl.H + 2) + fixed;
-        pl.full = V % 32 == 0;
+        pl.full = V % (32 * CH) == 0;
         lats[i].plan = pl;
         t_max = std::max(t_max, pl.threads);
         s_max = std::max(s_max, pl.smem);
         all_full = all_full && pl.full;
     }
     // shared by every batch: the device's whole opt-in shared memory
-    cudaError_t e = all_full ? cudaFuncSetAttribute(batch_update2<S, 1, true>,
+    cudaError_t e = all_full ? cudaFuncSetAttribute(batch_update2<S, CH, true>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)
-                             : cudaFuncSetAttribute(batch_update2<S, 1, false>,
+                             : cudaFuncSetAttribute(batch_update2<S, CH, false>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
     if (e != cudaSuccess) return false;
-    *threads = t_max;
-    *smem = s_max;
-    *full = all_full;
+    grp->ch = CH;
+    grp->threads = t_max;
+    grp->smem = s_max;
+    grp->full = all_full;
     return true;
 }
 
 template <typename S>
-cudaError_t launch_batch_for(bool full, const BatchLat *lats, const int *cta_lat, const int *cta_first,
-                             int total_ctas, int threads, size_t smem, const int *pt_lat, const long long *pt_begin,
+bool plan_batch_for(BatchLat *lats, int count, BatchTwoGroup *groups, int *ngroups) {
+    int dev = 0, smem_max = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    std::vector<int> one, two;
+    for (int i = 0; i < count; ++i) {
+        const Geometry &g = lats[i].g;
+        const int V = row_vectors<S>(g);
+        if (g.dim != 3 || g.driven || !V) return false;
+        if (Store<S>::W * 2 <= 8 && V > 32) two.push_back(i);
+        else one.push_back(i);
+    }
+    int n = 0;
+    if (!one.empty()) {
+        if (!plan_group<S, 1>(lats, one, smem_max, &groups[n])) return false;
+        ++n;
+    }
+    if constexpr (Store<S>::W * 2 <= 8)
+        if (!two.empty()) {
+            if (!plan_group<S, 2>(lats, two, smem_max, &groups[n])) return false;
+            ++n;
+        }
+    *ngroups = n;
+    return true;
+}
+
+template <typename S>
+cudaError_t launch_batch_for(const BatchTwoGroup *groups, int ngroups, const BatchLat *lats, const int *cta_lat,
+                             const int *cta_first, const int *pt_lat, const long long *pt_begin,
                              long long total_points, long long *step, unsigned *done, int sample_grid,
                              cudaStream_t s) {
     if (total_points > 0) {
@@ -850,32 +881,45 @@ cudaError_t launch_batch_for(bool full, const BatchLat *lats, const int *cta_lat
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    auto kernel = full ? batch_update2<S, 1, true> : batch_update2<S, 1, false>;
-    kernel<<<total_ctas, threads, smem, s>>>(lats, cta_lat, cta_first, step, done);
-    return cudaGetLastError();
+    for (int k = 0; k < ngroups; ++k) {
+        const BatchTwoGroup &G = groups[k];
+        const int adv = k == ngroups - 1;
+        if (G.ch == 1) {
+            auto kernel = G.full ? batch_update2<S, 1, true> : batch_update2<S, 1, false>;
+            kernel<<<G.ctas, G.threads, G.smem, s>>>(lats, cta_lat, cta_first, G.cta_begin, adv, step, done);
+        } else if constexpr (Store<S>::W * 2 <= 8) {
+            auto kernel = G.full ? batch_update2<S, 2, true> : batch_update2<S, 2, false>;
+            kernel<<<G.ctas, G.threads, G.smem, s>>>(lats, cta_lat, cta_first, G.cta_begin, adv, step, done);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
 
-bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, int *threads, size_t *smem, bool *full) {
+bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, BatchTwoGroup *groups, int *ngroups) {
     switch (p) {
-        case Prec::F16: return plan_batch_for<__half>(lats, count, threads, smem, full);
-        case Prec::F32: return plan_batch_for<float>(lats, count, threads, smem, full);
+        case Prec::F16: return plan_batch_for<__half>(lats, count, groups, ngroups);
+        case Prec::F32: return plan_batch_for<float>(lats, count, groups, ngroups);
         default: return false;
     }
 }
 
-cudaError_t launch_batch_two_steps(Prec p, bool full, const BatchLat *lats, const int *cta_lat, const int *cta_first,
-                                   int total_ctas, int threads, size_t smem, const int *pt_lat,
+cudaError_t launch_batch_two_steps(Prec p, const BatchTwoGroup *groups, int ngroups, const BatchLat *lats,
+                                   const int *cta_lat, const int *cta_first, const int *pt_lat,
                                    const long long *pt_begin, long long total_points, long long *step,
                                    unsigned *done, int sample_grid, cudaStream_t s) {
     switch (p) {
         case Prec::F16:
-            return launch_batch_for<__half>(full, lats, cta_lat, cta_first, total_ctas, threads, smem, pt_lat,
-                                            pt_begin, total_points, step, done, sample_grid, s);
+            return launch_batch_for<__half>(groups, ngroups, lats, cta_lat, cta_first, pt_lat, pt_begin,
+                                            total_points, step, done, sample_grid, s);
         case Prec::F32:
-            return launch_batch_for<float>(full, lats, cta_lat, cta_first, total_ctas, threads, smem, pt_lat,
-                                           pt_begin, total_points, step, done, sample_grid, s);
+            return launch_batch_for<float>(groups, ngroups, lats, cta_lat, cta_first, pt_lat, pt_begin,
+                                           total_points, step, done, sample_grid, s);
         default: return cudaErrorInvalidValue;
     }
 }
