@@ -291,6 +291,7 @@ struct wlb_batch {
     wlb::BatchTwoGroup groups[2];         // 3D: lane-layout groups, one launch each
     int ngroups = 0;
     int two_ch = 1;                       // 2D: chunks per lane of the widest row
+    int two_nx = 0;                       // 2D: widest row (staging slot size)
     int *d_cta_lat = nullptr, *d_cta_first = nullptr;
     char err[512] = {0};
 };
@@ -372,7 +373,7 @@ cudaError_t issue_steps(wlb_batch *b, int nsteps, int threads, int bps, cudaStre
                     ? wlb::launch_batch_two_steps(b->prec, b->groups, b->ngroups, b->d_lats, b->d_cta_lat,
                                                   b->d_cta_first, b->d_pt_lat, b->d_pt_begin, b->total_points,
                                                   b->d_step, b->d_done, grid, s)
-                    : wlb::launch_batch2d_two_steps(b->prec, b->two_ch, b->d_lats, b->d_cta_lat, b->d_cta_first,
+                    : wlb::launch_batch2d_two_steps(b->prec, b->two_ch, b->two_nx, b->d_lats, b->d_cta_lat, b->d_cta_first,
                                                     b->total_ctas, b->d_pt_lat, b->d_pt_begin, b->total_points,
                                                     b->d_step, b->d_done, grid, s);
             if (e != cudaSuccess) return e;
@@ -615,7 +616,8 @@ wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws
     int tasks2d = 0;
     const bool planned =
         even && (b->dim == 3 ? wlb::plan_batch_two_steps(b->prec, b->lat.data(), count, b->groups, &b->ngroups)
-                             : wlb::plan_batch2d_two_steps(b->prec, b->lat.data(), count, &tasks2d, &b->two_ch));
+                             : wlb::plan_batch2d_two_steps(b->prec, b->lat.data(), count, &tasks2d, &b->two_ch,
+                                                           &b->two_nx));
     if (planned) {
         // CTA (3D) or warp (2D) -> lattice table, the lattices of each 3D
         // lane-layout group together; first[i] = lattice i's first entry

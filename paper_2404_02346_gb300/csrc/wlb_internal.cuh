@@ -131,10 +131,10 @@ cudaError_t launch_batch_two_steps(Prec p, const BatchTwoGroup *groups, int ngro
 
 // The same for batches of 2D lattices (wlb_two_step_2d.cu): a warp sweeps a
 // chunk of rows of one lattice.  Plans every lattice (plan.zc rows per chunk,
-// plan.chunks chunks), returns the number of warps and the chunks per lane of
-// the widest row; false if some lattice cannot take it.
-bool plan_batch2d_two_steps(Prec p, BatchLat *lats, int count, int *tasks, int *chunks_per_lane);
-cudaError_t launch_batch2d_two_steps(Prec p, int chunks_per_lane, const BatchLat *lats, const int *task_lat,
+// plan.chunks chunks), returns the number of warps, the chunks per lane and
+// the length of the widest row; false if some lattice cannot take it.
+bool plan_batch2d_two_steps(Prec p, BatchLat *lats, int count, int *tasks, int *chunks_per_lane, int *nx_max);
+cudaError_t launch_batch2d_two_steps(Prec p, int chunks_per_lane, int nx_max, const BatchLat *lats, const int *task_lat,
                                      const int *task_first, int total_tasks, const int *pt_lat,
                                      const long long *pt_begin, long long total_points, long long *step,
                                      unsigned *done, int sample_grid, cudaStream_t s);

@@ -5,13 +5,15 @@
 // to t+2 (buffer B).  In 2D a lattice row needs no neighbour row of the same
 // time level besides those above and below it, so each warp sweeps a chunk of
 // rows ya .. yb-1 on its own: for p = ya-1 .. yb it computes S1 on row p from
-// A (rows p-1, p, p+1, read directly, one row ahead), then S2 on row p-1 from
-// its registers:
+// A (rows p-1, p, p+1, staged in the warp's shared-memory ring three rows
+// ahead by per-thread asynchronous copies), then S2 on row p-1 from its
+// registers:
 //   rest, +x, -x   from S1 of row p-1 (x shift by shuffles, periodic wrap),
 //   +y             from S1 of row p-2,
 //   -y             from S1 of row p.
-// No shared memory, no barrier, no warp waits for another; the rows just
-// outside a chunk are computed by both warps that need them.  The t+1 values
+// No barrier, no warp waits for another (each lane reads back only what it
+// copied); the rows just outside a chunk are computed by both warps that need
+// them.  The t+1 values
 // are rounded to the storage type as a stored state would be, so results are
 // bit-identical to two single steps.
 #include "wlb_handle.cuh"
@@ -22,6 +24,7 @@ namespace {
 
 constexpr int kRowsPerWarp = 32;   // row chunk of one warp (two halo rows per chunk)
 constexpr int kWarpsPerBlock = 2;  // small blocks: as many warps per SM as registers allow
+constexpr int kDepth = 3;          // rows staged ahead per warp (shared memory)
 
 // The value a stored state holds for v (storage rounding).
 template <typename S> __device__ __forceinline__ typename Store<S>::R as_stored(typename Store<S>::R v) { return v; }
@@ -58,9 +61,52 @@ __device__ __forceinline__ void row_shift(const R (&px)[CH][W], const R (&mx)[CH
     }
 }
 
+// Plain 16-byte shared-memory reads of W values of the storage type.
+template <typename S> struct StageVec;
+template <> struct StageVec<float> {
+    __device__ static void ld(const float *p, float (&v)[4]) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <> struct StageVec<double> {
+    __device__ static void ld(const double *p, double (&v)[2]) {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    }
+};
+template <> struct StageVec<__half> {
+    __device__ static void ld(const __half *p, float (&v)[8]) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(p);
+        const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h;
+            memcpy(&h, &w[i], 4);
+            const float2 f = __half22float2(h);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    }
+};
+
+// Per-thread asynchronous 16-byte copies global -> shared (each lane copies
+// exactly the vectors it reads back later, so waiting on its own groups is all
+// the synchronisation needed).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // The sweep of one row chunk of one lattice by one warp (warp-uniform flow).
+// `ring`: this warp's kDepth staging slots of the five rows S1 of a row pulls
+// (nxs values each).
 template <typename S, int CH>
-__device__ __forceinline__ void sweep_rows(const BatchLat &L, int chunk, long long t, int lane) {
+__device__ __forceinline__ void sweep_rows(const BatchLat &L, int chunk, long long t, int lane, S *ring, int nxs) {
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
     const int nx = L.g.n[0], ny = L.g.n[1];
@@ -78,46 +124,61 @@ __device__ __forceinline__ void sweep_rows(const BatchLat &L, int chunk, long lo
     for (int c = 0; c < CH; ++c) act[c] = c * 32 + lane < V;
     R n0[CH][W], n1[CH][W], n2[CH][W], cq[CH][W];  // S1 of row p-1: rest, +x, -x; its c^2
     R py0[CH][W], py1[CH][W];                      // +y of S1 rows p-2, p-1
-    // the values S1 of row p pulls and its class bytes, loaded one row ahead
-    R f[5][CH][W];
-    unsigned long long cl[CH];
-    auto load_row = [&](int p, R (&g)[5][CH][W], unsigned long long (&gc)[CH]) {
-        const int y = (p + ny) % ny, ym = (y + ny - 1) % ny, yp = (y + 1) % ny;
-        const long long r0 = (long long)y * nx;
+    // Stage the five rows S1 of row p pulls into slot (p - ya + 1) % kDepth;
+    // one commit group per row (empty past the chunk).
+    auto stage_row = [&](int p) {
+        if (p <= yb) {
+            const int y = (p + ny) % ny, ym = (y + ny - 1) % ny, yp = (y + 1) % ny;
+            const long long r0 = (long long)y * nx;
+            S *dst = ring + (size_t)((p - ya + 1) % kDepth) * 5 * nxs;
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int x0 = (c * 32 + lane) * W;
-            if (act[c]) {
-                Store<S>::load(A + r0 + x0, g[0][c]);
-                Store<S>::load(A + nc + r0 + x0, g[1][c]);
-                Store<S>::load(A + 2 * nc + r0 + x0, g[2][c]);
-                Store<S>::load(A + 3 * nc + (long long)ym * nx + x0, g[3][c]);
-                Store<S>::load(A + 4 * nc + (long long)yp * nx + x0, g[4][c]);
-                gc[c] = load_classes<W>(cls + r0 + x0);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 5; ++i)
-#pragma unroll
-                    for (int e = 0; e < W; ++e) g[i][c][e] = R(0);
-                gc[c] = 0;
+            for (int c = 0; c < CH; ++c) {
+                if (!act[c]) continue;
+                const int x0 = (c * 32 + lane) * W;
+                cp_async16(dst + x0, A + r0 + x0);
+                cp_async16(dst + nxs + x0, A + nc + r0 + x0);
+                cp_async16(dst + 2 * nxs + x0, A + 2 * nc + r0 + x0);
+                cp_async16(dst + 3 * nxs + x0, A + 3 * nc + (long long)ym * nx + x0);
+                cp_async16(dst + 4 * nxs + x0, A + 4 * nc + (long long)yp * nx + x0);
             }
         }
+        cp_async_commit();
     };
-    load_row(ya - 1, f, cl);
+    // class bytes of row p, one row ahead in registers
+    auto load_cls = [&](int p, unsigned long long (&gc)[CH]) {
+        const long long r0 = (long long)((p + ny) % ny) * nx;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) gc[c] = act[c] ? load_classes<W>(cls + r0 + (c * 32 + lane) * W) : 0ull;
+    };
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d) stage_row(ya - 1 + d);
+    unsigned long long cl[CH];
+    load_cls(ya - 1, cl);
     for (int k = 0, p = ya - 1; p <= yb; ++k, ++p) {
         const int y = (p + ny) % ny;
         const long long r0 = (long long)y * nx;
-        R fn[5][CH][W];
         unsigned long long cln[CH];
-        if (p < yb) load_row(p + 1, fn, cln);
+        if (p < yb) load_cls(p + 1, cln);
+        cp_async_wait<kDepth - 1>();  // this lane's copies of row p have landed
+        const S *st = ring + (size_t)(k % kDepth) * 5 * nxs;
+        R f[5][CH][W];
         R cs[CH][W];
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             const int x0 = (c * 32 + lane) * W;
+            if (act[c]) {
+#pragma unroll
+                for (int i = 0; i < 5; ++i) StageVec<S>::ld(st + (size_t)i * nxs + x0, f[i][c]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 5; ++i)
+#pragma unroll
+                    for (int e = 0; e < W; ++e) f[i][c][e] = R(0);
+            }
 #pragma unroll
             for (int e = 0; e < W; ++e) {  // the c^2 of the one-step kernels
                 const unsigned kc = (unsigned)(cl[c] >> (8 * e)) & 0xffu;
-                cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : c2f[r0 + x0 + e]);
+                cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : (act[c] ? c2f[r0 + x0 + e] : c0sq));
             }
         }
         R fpx[CH][W], fmx[CH][W];
@@ -155,8 +216,10 @@ __device__ __forceinline__ void sweep_rows(const BatchLat &L, int chunk, long lo
                 for (int i = 0; i < 5; ++i) Store<S>::store(B + i * nc + rq + x0, out[i]);
             }
         }
+        stage_row(p + kDepth);  // refill the slot just read (its values are in registers)
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
+        for (int c = 0; c < CH; ++c) {
+            if (p < yb) cl[c] = cln[c];
 #pragma unroll
             for (int e = 0; e < W; ++e) {
                 py0[c][e] = py1[c][e];
@@ -166,17 +229,9 @@ __device__ __forceinline__ void sweep_rows(const BatchLat &L, int chunk, long lo
                 n2[c][e] = o[2][c][e];
                 cq[c][e] = cs[c][e];
             }
-        if (p < yb) {
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                cl[c] = cln[c];
-#pragma unroll
-                for (int i = 0; i < 5; ++i)
-#pragma unroll
-                    for (int e = 0; e < W; ++e) f[i][c][e] = fn[i][c][e];
-            }
         }
     }
+    cp_async_wait<0>();
 }
 
 // One launch: warp w sweeps chunk w - task_first[i] of lattice i = task_lat[w]
@@ -187,15 +242,17 @@ template <typename S, int CH>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) batch2d_update2(const BatchLat *__restrict__ lats,
                                                                        const int *__restrict__ task_lat,
                                                                        const int *__restrict__ task_first,
-                                                                       int total_tasks, long long *step,
-                                                                       unsigned *done) {
+                                                                       int total_tasks, int nxs,
+                                                                       long long *step, unsigned *done) {
+    extern __shared__ __align__(16) unsigned char smem2d[];
     const long long t = *step;
     const int lane = threadIdx.x & 31;
     const int task = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (task < total_tasks) {
         const int i = task_lat[task];
         const BatchLat &L = lats[i];
-        if (t < L.n_steps) sweep_rows<S, CH>(L, task - task_first[i], t, lane);  // warp-uniform
+        S *ring = reinterpret_cast<S *>(smem2d) + (size_t)(threadIdx.x >> 5) * kDepth * 5 * nxs;
+        if (t < L.n_steps) sweep_rows<S, CH>(L, task - task_first[i], t, lane, ring, nxs);  // warp-uniform
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -285,9 +342,9 @@ __global__ void __launch_bounds__(256) batch2d_sample_two(const BatchLat *__rest
 }
 
 template <typename S>
-bool plan_for(BatchLat *lats, int count, int *tasks, int *chunks_per_lane) {
+bool plan_for(BatchLat *lats, int count, int *tasks, int *chunks_per_lane, int *nx_max) {
     constexpr int W = Store<S>::W;
-    int ch = 1, total = 0;
+    int ch = 1, total = 0, wide = 0;
     for (int i = 0; i < count; ++i) {
         const Geometry &g = lats[i].g;
         if (g.dim != 2 || g.driven || g.n[0] % W) return false;
@@ -295,6 +352,7 @@ bool plan_for(BatchLat *lats, int count, int *tasks, int *chunks_per_lane) {
         const int c = (V + 31) / 32;
         if (c > 2 || W * c > 8) return false;  // at most 8 values per lane
         ch = c > ch ? c : ch;
+        wide = g.n[0] > wide ? g.n[0] : wide;
         TwoStepPlan pl;
         pl.zc = g.n[1] < kRowsPerWarp ? g.n[1] : kRowsPerWarp;
         pl.chunks = (g.n[1] + pl.zc - 1) / pl.zc;
@@ -308,13 +366,14 @@ bool plan_for(BatchLat *lats, int count, int *tasks, int *chunks_per_lane) {
     }
     *tasks = total;
     *chunks_per_lane = ch;
+    *nx_max = wide;
     return true;
 }
 
 template <typename S>
-cudaError_t launch_for(int ch, const BatchLat *lats, const int *task_lat, const int *task_first, int total_tasks,
-                       const int *pt_lat, const long long *pt_begin, long long total_points, long long *step,
-                       unsigned *done, int sample_grid, cudaStream_t s) {
+cudaError_t launch_for(int ch, int nx_max, const BatchLat *lats, const int *task_lat, const int *task_first,
+                       int total_tasks, const int *pt_lat, const long long *pt_begin, long long total_points,
+                       long long *step, unsigned *done, int sample_grid, cudaStream_t s) {
     if (total_points > 0) {
         const long long need = (total_points + 255) / 256;
         const int g = (int)(need < sample_grid ? need : sample_grid);
@@ -324,36 +383,41 @@ cudaError_t launch_for(int ch, const BatchLat *lats, const int *task_lat, const 
     }
     const int blocks = (total_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int threads = 32 * kWarpsPerBlock;
-    if (ch == 1) batch2d_update2<S, 1><<<blocks, threads, 0, s>>>(lats, task_lat, task_first, total_tasks, step, done);
+    // per warp: kDepth slots of five rows of the widest lattice (<= 30 KB a block)
+    const size_t smem = (size_t)kWarpsPerBlock * kDepth * 5 * nx_max * sizeof(S);
+    if (ch == 1)
+        batch2d_update2<S, 1><<<blocks, threads, smem, s>>>(lats, task_lat, task_first, total_tasks, nx_max, step,
+                                                             done);
     else if constexpr (Store<S>::W * 2 <= 8)
-        batch2d_update2<S, 2><<<blocks, threads, 0, s>>>(lats, task_lat, task_first, total_tasks, step, done);
+        batch2d_update2<S, 2><<<blocks, threads, smem, s>>>(lats, task_lat, task_first, total_tasks, nx_max, step,
+                                                             done);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool plan_batch2d_two_steps(Prec p, BatchLat *lats, int count, int *tasks, int *chunks_per_lane) {
+bool plan_batch2d_two_steps(Prec p, BatchLat *lats, int count, int *tasks, int *chunks_per_lane, int *nx_max) {
     switch (p) {
-        case Prec::F16: return plan_for<__half>(lats, count, tasks, chunks_per_lane);
-        case Prec::F64: return plan_for<double>(lats, count, tasks, chunks_per_lane);
-        default: return plan_for<float>(lats, count, tasks, chunks_per_lane);
+        case Prec::F16: return plan_for<__half>(lats, count, tasks, chunks_per_lane, nx_max);
+        case Prec::F64: return plan_for<double>(lats, count, tasks, chunks_per_lane, nx_max);
+        default: return plan_for<float>(lats, count, tasks, chunks_per_lane, nx_max);
     }
 }
 
-cudaError_t launch_batch2d_two_steps(Prec p, int chunks_per_lane, const BatchLat *lats, const int *task_lat,
+cudaError_t launch_batch2d_two_steps(Prec p, int chunks_per_lane, int nx_max, const BatchLat *lats, const int *task_lat,
                                      const int *task_first, int total_tasks, const int *pt_lat,
                                      const long long *pt_begin, long long total_points, long long *step,
                                      unsigned *done, int sample_grid, cudaStream_t s) {
     switch (p) {
         case Prec::F16:
-            return launch_for<__half>(chunks_per_lane, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
+            return launch_for<__half>(chunks_per_lane, nx_max, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
                                       total_points, step, done, sample_grid, s);
         case Prec::F64:
-            return launch_for<double>(chunks_per_lane, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
+            return launch_for<double>(chunks_per_lane, nx_max, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
                                       total_points, step, done, sample_grid, s);
         default:
-            return launch_for<float>(chunks_per_lane, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
+            return launch_for<float>(chunks_per_lane, nx_max, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
                                      total_points, step, done, sample_grid, s);
     }
 }
