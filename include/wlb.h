@@ -364,15 +364,17 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
  * of both steps (t from the stored state, t+1 recomputed from it by the same
  * arithmetic), in the order two single steps add them.  On by default (set
  * up by wlb_create with an automatic slab height) wherever it is supported:
- * 3D, periodic boundaries, FP32 or FP16 storage, nx a multiple of 128 (FP32)
- * or 256 (FP16) cells, each row split into warp-wide segments, and at least
- * one slab row fitting the shared memory (nx up to about 1500 FP32 cells).
+ * 3D, periodic boundaries, FP32 or FP16 storage, nx a multiple of 16 cells
+ * (each row split into warp-wide segments, the last one possibly shorter),
+ * and at least one slab row fitting the shared memory (nx up to about 1500
+ * FP32 cells).
  * Elsewhere, or with enable = 0, every step is one launch.  enable: 0 off;
  * 1 on, lane layout chosen by the library; 2 on with one 16-byte chunk per
  * lane (more, lighter warps); 3 on with two (WLB_ERR_ARG if unsupported).
- * slab_rows: 0 lets the library choose (largest slab the shared memory
- * holds, z chunked to fill the SMs), else that height (WLB_ERR_ARG if it does
- * not fit; the setting is then unchanged).  A stalled staging copy (bounded
+ * slab_rows: 0 lets the library choose (by estimated time: slab height and
+ * z chunks that fill the SMs, the tallest among near-equal estimates), else
+ * that height (WLB_ERR_ARG if it does not fit; the setting is then
+ * unchanged).  A stalled staging copy (bounded
  * wait) makes wlb_force return WLB_ERR_TIMEOUT.  The paper has no counterpart:
  * it is a memory-traffic optimisation of the same update. */
 wlb_status wlb_set_two_step(wlb_handle *h, int enable, int slab_rows);
