@@ -368,6 +368,9 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
  * (each row split into warp-wide segments, the last one possibly shorter),
  * and at least one slab row fitting the shared memory (nx up to about 1500
  * FP32 cells).
+ * 2D lattices (periodic, any storage, rows of at most two 16-byte chunks
+ * per lane and 8 values per lane) take it too: each warp sweeps a chunk of
+ * rows, both steps in its registers (slab_rows must be 0).
  * Elsewhere, or with enable = 0, every step is one launch.  enable: 0 off;
  * 1 on, lane layout chosen by the library; 2 on with one 16-byte chunk per
  * lane (more, lighter warps); 3 on with two (WLB_ERR_ARG if unsupported).

@@ -135,6 +135,24 @@ void destroy_graphs(wlb_handle *h) {
     }
 }
 
+// One launch of two steps from buffer src (3D slab kernel or 2D row sweep).
+cudaError_t two_steps(wlb_handle *h, int src, bool sampled, cudaStream_t s) {
+    if (h->g.dim == 2) return wlb::launch_two_steps_2d(h->g, h->b, h->prec, h->two_plan, src, sampled, s);
+    return wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, src, sampled, h->b.err, s, h->side);
+}
+
+// Whether, and with which plan, a handle can take two steps per launch.
+bool two_step_plan(const wlb_handle *h, int slab_rows, int mode, wlb::TwoStepPlan *plan, cudaError_t *err) {
+    if (h->g.dim == 2) {
+        if (!wlb::two_step_2d_supported(h->g, h->prec) || slab_rows != 0) return false;
+        *err = wlb::plan_two_steps_2d(h->g, h->prec, plan);
+        return true;
+    }
+    if (!wlb::two_step_supported(h->g, h->prec)) return false;
+    *err = wlb::plan_two_steps(h->g, h->prec, slab_rows, mode, plan);
+    return true;
+}
+
 // Update launches in one period: each flips the population buffer.
 long long period_launches(const wlb_handle *h, bool) {
     return h->two_step ? h->period / 2 + h->period % 2 : h->period;
@@ -146,7 +164,7 @@ cudaError_t issue_period(wlb_handle *h, int start, bool sampled, cudaStream_t s)
     long long t = 0;
     if (h->two_step)
         for (; t + 1 < h->period; t += 2) {  // two steps per launch
-            cudaError_t e = wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, cur, sampled, h->b.err, s, h->side);
+            cudaError_t e = two_steps(h, cur, sampled, s);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -294,8 +312,10 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
         return WLB_ERR_CUDA;
     }
     // steps two per launch wherever the kernel applies (bit-identical)
-    if (wlb::two_step_supported(h->g, h->prec) && wlb::plan_two_steps(h->g, h->prec, 0, 1, &h->two_plan) == cudaSuccess)
-        h->two_step = true;
+    {
+        cudaError_t pe = cudaSuccess;
+        if (two_step_plan(h, 0, 1, &h->two_plan, &pe) && pe == cudaSuccess) h->two_step = true;
+    }
     cudaGetLastError();
     *out = h;
     return WLB_OK;
@@ -330,8 +350,7 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
             continue;
         }
         if (h->two_step && n >= 2 && (!sampled || h->samples_in_period + 2 <= h->period)) {
-            WLB_CUDA(h, wlb::launch_two_steps(h->g, h->b, h->prec, h->two_plan, h->src, sampled, h->b.err, h->stream,
-                                              h->side),
+            WLB_CUDA(h, two_steps(h, h->src, sampled, h->stream),
                      "two-step kernels");
             h->src ^= 1;
             h->steps_done += 2;
@@ -444,11 +463,13 @@ wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out) {
 wlb_status wlb_set_two_step(wlb_handle *h, int enable, int slab_rows) {
     if (!h || slab_rows < 0 || enable < 0 || enable > 3) return WLB_ERR_ARG;
     DeviceGuard dg(h->device);
-    if (enable && !wlb::two_step_supported(h->g, h->prec))
-        return fail(h, WLB_ERR_ARG, "two steps per launch need a 3D periodic FP32/FP16 lattice of warp-wide rows");
     wlb::TwoStepPlan plan;
     if (enable) {
-        cudaError_t e = wlb::plan_two_steps(h->g, h->prec, slab_rows, enable, &plan);
+        cudaError_t e = cudaSuccess;
+        if (!two_step_plan(h, slab_rows, enable, &plan, &e))
+            return fail(h, WLB_ERR_ARG,
+                        "two steps per launch need a periodic lattice: 3D FP32/FP16 rows of 16-cell multiples, or 2D "
+                        "rows of at most 8 values per lane (no slab height)");
         if (e != cudaSuccess) return fail(h, WLB_ERR_ARG, "slab height or lane layout does not fit", e);
     }
     const bool same = (enable != 0) == h->two_step && plan.H == h->two_plan.H && plan.zc == h->two_plan.zc &&

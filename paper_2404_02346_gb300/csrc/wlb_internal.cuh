@@ -129,6 +129,15 @@ cudaError_t launch_batch_two_steps(Prec p, const BatchTwoGroup *groups, int ngro
                                    const long long *pt_begin, long long total_points, long long *step,
                                    unsigned *done, int sample_grid, cudaStream_t s);
 
+// Two steps per launch for a single 2D lattice (wlb_two_step_2d.cu): periodic,
+// rows of at most two 16-byte chunks (8 values) per lane; each warp sweeps a
+// chunk of plan.zc rows (plan.chunks chunks).  From buffer src into src ^ 1;
+// with sample, a sampling kernel before the update adds both steps' sums.
+bool two_step_2d_supported(const Geometry &g, Prec p);
+cudaError_t plan_two_steps_2d(const Geometry &g, Prec p, TwoStepPlan *out);
+cudaError_t launch_two_steps_2d(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src,
+                                bool sample, cudaStream_t s);
+
 // The same for batches of 2D lattices (wlb_two_step_2d.cu): a warp sweeps a
 // chunk of rows of one lattice.  Plans every lattice (plan.zc rows per chunk,
 // plan.chunks chunks), returns the number of warps, the chunks per lane and

@@ -102,23 +102,52 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// One 2D lattice as a row sweep sees it.
+template <typename S>
+struct Rows2D {
+    const S *A;  // state t
+    S *B;        // state t + 2
+    const uint8_t *cls;
+    const typename Store<S>::R *c2f;
+    int nx, ny;
+    long long ncell;
+    typename Store<S>::R c0sq, cpsq;
+    int yc;  // rows per warp chunk
+};
+
+template <typename S>
+__host__ __device__ inline Rows2D<S> rows2d(const Geometry &g, const Buffers &b, int src, int yc) {
+    using R = typename Store<S>::R;
+    Rows2D<S> P;
+    P.A = (const S *)b.pop[src];
+    P.B = (S *)b.pop[src ^ 1];
+    P.cls = b.cls;
+    P.c2f = (const R *)b.c2;
+    P.nx = g.n[0];
+    P.ny = g.n[1];
+    P.ncell = g.ncell;
+    P.c0sq = (R)(g.c0 * g.c0);
+    P.cpsq = (R)(g.cp * g.cp);
+    P.yc = yc;
+    return P;
+}
+
 // The sweep of one row chunk of one lattice by one warp (warp-uniform flow).
 // `ring`: this warp's kDepth staging slots of the five rows S1 of a row pulls
 // (nxs values each).
 template <typename S, int CH>
-__device__ __forceinline__ void sweep_rows(const BatchLat &L, int chunk, long long t, int lane, S *ring, int nxs) {
+__device__ __forceinline__ void sweep_rows(const Rows2D<S> &P, int chunk, int lane, S *ring, int nxs) {
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
-    const int nx = L.g.n[0], ny = L.g.n[1];
-    const long long nc = L.g.ncell;
-    const int V = nx / W, yc = L.plan.zc;
+    const int nx = P.nx, ny = P.ny;
+    const long long nc = P.ncell;
+    const int V = nx / W, yc = P.yc;
     const int ya = chunk * yc, yb = min(ny, ya + yc);
-    const int src = (int)((t >> 1) & 1);
-    const S *__restrict__ A = (const S *)L.b.pop[src];
-    S *__restrict__ B = (S *)L.b.pop[src ^ 1];
-    const uint8_t *__restrict__ cls = L.b.cls;
-    const R *__restrict__ c2f = (const R *)L.b.c2;
-    const R c0sq = (R)(L.g.c0 * L.g.c0), cpsq = (R)(L.g.cp * L.g.cp);
+    const S *__restrict__ A = P.A;
+    S *__restrict__ B = P.B;
+    const uint8_t *__restrict__ cls = P.cls;
+    const R *__restrict__ c2f = P.c2f;
+    const R c0sq = P.c0sq, cpsq = P.cpsq;
     bool act[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) act[c] = c * 32 + lane < V;
@@ -252,7 +281,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) batch2d_update2(const Bat
         const int i = task_lat[task];
         const BatchLat &L = lats[i];
         S *ring = reinterpret_cast<S *>(smem2d) + (size_t)(threadIdx.x >> 5) * kDepth * 5 * nxs;
-        if (t < L.n_steps) sweep_rows<S, CH>(L, task - task_first[i], t, lane, ring, nxs);  // warp-uniform
+        if (t < L.n_steps)  // warp-uniform
+            sweep_rows<S, CH>(rows2d<S>(L.g, L.b, (int)((t >> 1) & 1), L.plan.zc), task - task_first[i], lane, ring,
+                              nxs);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -341,6 +372,67 @@ __global__ void __launch_bounds__(256) batch2d_sample_two(const BatchLat *__rest
     }
 }
 
+// A single 2D lattice (a handle): warp w sweeps row chunk w.
+template <typename S, int CH>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) update2_rows2d(Rows2D<S> P, int chunks, int nxs) {
+    extern __shared__ __align__(16) unsigned char smem2d[];
+    const int lane = threadIdx.x & 31;
+    const int task = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (task >= chunks) return;  // whole warp; the sweep has no block barrier
+    S *ring = reinterpret_cast<S *>(smem2d) + (size_t)(threadIdx.x >> 5) * kDepth * 5 * nxs;
+    sweep_rows<S, CH>(P, task, lane, ring, nxs);
+}
+
+// Its sampling of both steps of a launch, one thread per point, in the order
+// of two single steps (the handle folds at period ends).
+template <typename S>
+__global__ void __launch_bounds__(256) sample_two_2d(Geometry g, const int4 *__restrict__ st_xyz,
+                                                     const typename Store<S>::R *__restrict__ st_w,
+                                                     const typename Store<S>::R *__restrict__ nrm,
+                                                     typename Store<S>::R *acc, const S *__restrict__ A,
+                                                     const typename Store<S>::R *__restrict__ c2f) {
+    using R = typename Store<S>::R;
+    const int k = (int)((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (k >= g.n_surface) return;
+    sample_point_2d_thread(g, st_xyz, st_w, nrm, acc, k, [&](int x, int y, int z, R &rho, R(&J)[3]) {
+        pulled_moments(g, A, x, y, z, rho, J);
+    });
+    sample_point_2d_thread(g, st_xyz, st_w, nrm, acc, k, [&](int x, int y, int, R &rho, R(&J)[3]) {
+        moments_next_2d(g, A, c2f, x, y, rho, J);
+    });
+}
+
+// Chunks per lane for a 2D row of nx cells: 0 if it is not a whole number of
+// 16-byte vectors or needs more than two chunks / eight values per lane.
+template <typename S>
+int chunks_2d(int nx) {
+    constexpr int W = Store<S>::W;
+    if (nx % W) return 0;
+    const int c = (nx / W + 31) / 32;
+    return (c <= 2 && W * c <= 8) ? c : 0;
+}
+
+template <typename S>
+cudaError_t launch_single(const Geometry &g, const Buffers &b, const TwoStepPlan &pl, int src, bool sample,
+                          cudaStream_t s) {
+    using R = typename Store<S>::R;
+    if (sample && g.n_surface > 0) {
+        sample_two_2d<S><<<(g.n_surface + 255) / 256, 256, 0, s>>>(g, b.st_xyz, (const R *)b.st_w, (const R *)b.nrm,
+                                                                   (R *)b.acc, (const S *)b.pop[src],
+                                                                   (const R *)b.c2);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const Rows2D<S> P = rows2d<S>(g, b, src, pl.zc);
+    const int blocks = (pl.chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (pl.chunks_per_lane == 1)
+        update2_rows2d<S, 1><<<blocks, pl.threads, pl.smem, s>>>(P, pl.chunks, g.n[0]);
+    else if constexpr (Store<S>::W * 2 <= 8)
+        update2_rows2d<S, 2><<<blocks, pl.threads, pl.smem, s>>>(P, pl.chunks, g.n[0]);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 template <typename S>
 bool plan_for(BatchLat *lats, int count, int *tasks, int *chunks_per_lane, int *nx_max) {
     constexpr int W = Store<S>::W;
@@ -419,6 +511,49 @@ cudaError_t launch_batch2d_two_steps(Prec p, int chunks_per_lane, int nx_max, co
         default:
             return launch_for<float>(chunks_per_lane, nx_max, lats, task_lat, task_first, total_tasks, pt_lat, pt_begin,
                                      total_points, step, done, sample_grid, s);
+    }
+}
+
+bool two_step_2d_supported(const Geometry &g, Prec p) {
+    if (g.dim != 2 || g.driven) return false;
+    switch (p) {
+        case Prec::F16: return chunks_2d<__half>(g.n[0]) > 0;
+        case Prec::F64: return chunks_2d<double>(g.n[0]) > 0;
+        default: return chunks_2d<float>(g.n[0]) > 0;
+    }
+}
+
+cudaError_t plan_two_steps_2d(const Geometry &g, Prec p, TwoStepPlan *out) {
+    if (!two_step_2d_supported(g, p)) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const size_t bytes = p == Prec::F16 ? 2 : (p == Prec::F64 ? 8 : 4);
+    TwoStepPlan pl;
+    pl.chunks_per_lane = p == Prec::F16 ? chunks_2d<__half>(g.n[0])
+                                        : (p == Prec::F64 ? chunks_2d<double>(g.n[0]) : chunks_2d<float>(g.n[0]));
+    // rows per warp: up to kRowsPerWarp, fewer on short lattices so that
+    // every SM gets work (at least 4: two of the rows are halo)
+    const int per_sm = g.n[1] / (sms > 0 ? sms : 1);
+    pl.zc = per_sm < 4 ? 4 : (per_sm > kRowsPerWarp ? kRowsPerWarp : per_sm);
+    if (pl.zc > g.n[1]) pl.zc = g.n[1];
+    pl.chunks = (g.n[1] + pl.zc - 1) / pl.zc;
+    pl.H = pl.zc;
+    pl.nslab = 1;
+    pl.nseg = 1;
+    pl.threads = 32 * kWarpsPerBlock;
+    pl.smem = (size_t)kWarpsPerBlock * kDepth * 5 * g.n[0] * bytes;
+    *out = pl;
+    return cudaSuccess;
+}
+
+cudaError_t launch_two_steps_2d(const Geometry &g, const Buffers &b, Prec p, const TwoStepPlan &pl, int src,
+                                bool sample, cudaStream_t s) {
+    switch (p) {
+        case Prec::F16: return launch_single<__half>(g, b, pl, src, sample, s);
+        case Prec::F64: return launch_single<double>(g, b, pl, src, sample, s);
+        default: return launch_single<float>(g, b, pl, src, sample, s);
     }
 }
 

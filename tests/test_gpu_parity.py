@@ -359,6 +359,30 @@ def test_two_step_is_bit_identical(wlb, shape, lam, precision, rows, cpl, segmen
         assert np.array_equal(out[0][2], o[2])
 
 
+@pytest.mark.parametrize("shape,lam,precision", [
+    ((128, 128), 64.0, "f64"),   # the 2D cylinder workload's lattice and storage
+    ((192, 96), 48.0, "f32"),    # 48 vectors: two chunks per lane, 16 lanes idle in the second
+    ((128, 64), 32.0, "f16"),    # one chunk of eight halves per lane
+    ((64, 32), 16.0, "f32"),     # short lattice: 4-row chunks
+])
+def test_two_step_2d_is_bit_identical(wlb, shape, lam, precision):
+    """2D row sweep (two steps per launch, default) against one step per
+    launch: forces and fields equal bit for bit; odd tail of direct steps."""
+    prob = workloads.problem(2, shape, 1, lam, 4.0, (shape[0] / 2 + 0.25, lam / 8), cp=0.32, n_surface=64,
+                             n_periods=5, n_avg_periods=2)
+    out = []
+    for enable in (True, False):
+        with wlb.Solver(prob, precision=precision) as s:
+            s.set_two_step(enable)
+            assert s.info().steps_per_launch == (2 if enable else 1)
+            F = s.run()
+            s.step(5)
+            p1, u1 = s.fields()
+            out.append((F, p1, u1))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
 def test_two_step_odd_period_and_split_calls(wlb):
     """Odd period T = 25 (a single step closes every period and a two-step
     launch never crosses a fold) and sampled/unsampled calls of odd lengths:
@@ -412,8 +436,8 @@ def test_two_step_benchmark_lattice(wlb):
 
 
 def test_two_step_rejected_where_unsupported(wlb):
-    p2 = workloads.problem(2, (128, 64), 1, 32.0, 4.0, (64.0, 4.0), cp=0.375, n_surface=16,
-                           n_periods=2, n_avg_periods=1)
+    p2 = workloads.problem(2, (1024, 64), 1, 32.0, 4.0, (512.0, 4.0), cp=0.375, n_surface=16,
+                           n_periods=2, n_avg_periods=1)  # 2D rows of 256 vectors: too wide
     p3 = workloads.problem(3, (128, 32, 32), 2, 16.0, 3.0, (64.0, 16.0, 2.0), cp=0.42, n_surface=16,
                            n_periods=2, n_avg_periods=1)
     p3odd = workloads.problem(3, (100, 32, 32), 2, 16.0, 3.0, (50.0, 16.0, 2.0), cp=0.42, n_surface=16,
