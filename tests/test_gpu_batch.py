@@ -74,6 +74,9 @@ def test_batch_2d_ragged(wlb, precision):
         with wlb.Solver(p) as s:
             Fs = s.run()
         assert np.array_equal(F[i], Fs), (i, F[i], Fs)
+    if precision == "f32":  # the two-step 2D batch against the FP64 oracle directly
+        o = oracle.run(probs[1])["force"]
+        assert abs(F[1, 1] - o[1]) <= 1e-3 * abs(o[1]), (F[1], o)
 
 
 def test_batch_autotune_and_member_without_window(wlb):
@@ -127,6 +130,11 @@ def test_batch_two_steps_per_launch_bit_identical(wlb, precision):
         with wlb.Solver(p) as s:
             Fs = s.run()
         assert np.array_equal(F2[i], Fs), (i, F2[i], Fs)
+    if precision == "f32":  # and against the FP64 oracle directly (one- and two-chunk lattices)
+        for i in (0, 2):
+            o = oracle.run(probs[i])["force"]
+            ax = probs[i]["wave_axis"]
+            assert abs(F2[i, ax] - o[ax]) <= 1e-3 * abs(o[ax]), (i, F2[i], o)
 
 
 def test_batch_two_step_unavailable(wlb):
