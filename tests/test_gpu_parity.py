@@ -102,6 +102,38 @@ def test_sphere_256_full_size_short_run(wlb):
     _compare(short, g, o, p1_tol=1e-5, force_rtol=1e-4)
 
 
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+def test_sphere_512_full_size_short_run(wlb):
+    """The 512^3 sweep lattice (R = 24, 4096 points, a position with a large
+    force) in the launch configuration the sweep times (two steps per launch,
+    rows of two warps), for 8 steps with 4 sampled: classes and points
+    bit-exact, force within tolerance of the oracle."""
+    if _mem_available_gb() < 48:
+        pytest.skip("the FP64 oracle of a 512^3 lattice needs about 16 GB of host memory")
+    prob = workloads.sphere_3d_large(position=4)
+    short = dict(prob, n_steps=8, n_window=4)
+    o = oracle.run(short)
+    with wlb.Solver(prob) as s:
+        info = s.info()
+        assert info.steps_per_launch == 2 and info.two_step_segments == 2
+        s.init()
+        s.step(4, sample=False)
+        s.step(4, sample=True)
+        F = s.force()
+        g = {"force": F, "mask": s.mask(), "points": s.surface()}
+    _compare(short, g, o, p1_tol=None, force_rtol=1e-4)
+
+
 def test_sphere_256_full_length_uniform_medium_closed_form(wlb):
     """Full size and full length (256^3, 15360 steps, the benchmark's launch
     configuration) with cp = c0: the field must stay the closed-form lattice mode
