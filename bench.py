@@ -437,12 +437,22 @@ def run_surrogate(args):
     for _ in range(args.warmup):
         sur.predict(q)
     torch.cuda.synchronize()
+    # each call: one fused-forward launch plus a 4-byte status read, on the current stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for s in range(args.steps):
+        ev[2 * s].record()
         sur.predict(q)
+        ev[2 * s + 1].record()
     torch.cuda.synchronize()
     q_s = (time.perf_counter() - t0) / args.steps
+    k_s = sum(ev[2 * s].elapsed_time(ev[2 * s + 1]) for s in range(args.steps)) / args.steps * 1e-3
     sur.close()
+    # algorithmic products: 2 (4*256 + 2*256*256 + 256) flops per query
+    flops = 2.0 * (4 * 256 + 2 * 256 * 256 + 256) * (1 << 20)
+    peaks = _peaks()
+    peak = peaks.get("bf16_tflops") if peaks else None
+    achieved = flops / k_s / 1e12
     lb_rate = (len(train) + len(val)) / lb_s
     line = {
         "metric": "radiation forces/s, learned surrogate", "value": (1 << 20) / q_s, "unit": "forces/s",
@@ -452,6 +462,11 @@ def run_surrogate(args):
         "config": {"workload": "MLP 4-256-256-256-1 GELU; 20k train / 2k held-out 2D lattice forces "
                                "(192^2 D2Q5, 25 periods); 1M seeded queries",
                    "epochs": args.epochs, "batch": 512},
+        "roofline": {"bound": "tensor", "kernel": "mlp_forward_fused", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                     "traffic": None, "peak_source": "measured bf16_tflops (burst)" if peak else None,
+                     "kernel_ms": k_s * 1e3},
+        "gpu_launches": args.steps,
         "lattice_forces_per_s_batched": lb_rate,
         "speedup_vs_batched_lattice": (1 << 20) / q_s / lb_rate,
         "train_s": train_s, "final_train_loss": float(hist[-1]),

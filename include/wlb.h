@@ -336,6 +336,15 @@ wlb_status wlb_batch_destroy(wlb_batch *b);
  *                        mean batch loss.
  *   wlb_mlp_predict      x: device n x 4, y: device n FP32, inside: device n
  *                        bytes (may be NULL): 1 if the query lies in the box.
+ *                        Any n >= 0 (not bounded by batch_max; x and y may be
+ *                        NULL when n = 0).  By default
+ *                        one persistent kernel runs the whole network per
+ *                        128-query tile with the activations in shared and
+ *                        tensor memory and the weights streamed from L2.
+ *   wlb_mlp_set_fused    fused = 1 (default): predict as above; 0: one
+ *                        tensor-core GEMM launch per layer through device
+ *                        memory in batch_max chunks (the training forward).
+ *                        Both give the same bits.  WLB_ERR_ARG otherwise.
  * All calls synchronise the stream before returning.  WLB_ERR_TIMEOUT if a
  * tensor-core completion wait gave up (the kernel returns instead of hanging).
  */
@@ -349,6 +358,7 @@ wlb_status wlb_mlp_loss_grad(wlb_mlp *m, const float *x, const float *t, int n, 
 wlb_status wlb_mlp_train(wlb_mlp *m, const float *x, const float *t, long long n, int epochs, int batch, float lr,
                          float lr_final, unsigned long long seed, float *loss_history);
 wlb_status wlb_mlp_predict(wlb_mlp *m, const float *x, long long n, float *y, unsigned char *inside);
+wlb_status wlb_mlp_set_fused(wlb_mlp *m, int fused);
 const char *wlb_mlp_last_error(const wlb_mlp *m);
 wlb_status wlb_mlp_destroy(wlb_mlp *m);
 

@@ -115,6 +115,7 @@ _SIGNATURES = {
     "wlb_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)]),
     "wlb_mlp_predict": (ctypes.c_int, [_VP, _VP, ctypes.c_longlong, _VP, _VP]),
+    "wlb_mlp_set_fused": (ctypes.c_int, [_VP, ctypes.c_int]),
     "wlb_mlp_last_error": (ctypes.c_char_p, [_VP]),
     "wlb_mlp_destroy": (ctypes.c_int, [_VP]),
     "wlb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -399,6 +400,11 @@ class MLP:
                                          int(x.shape[0]), int(epochs), int(batch), float(lr), float(lr_final),
                                          int(seed), hist.ctypes.data_as(_FP)), "wlb_mlp_train")
         return hist
+
+    def set_fused(self, fused):
+        """True (default): predict with the one-launch fused network; False:
+        one GEMM launch per layer (the training forward)."""
+        self._mcheck(lib().wlb_mlp_set_fused(self._h, 1 if fused else 0), "wlb_mlp_set_fused")
 
     def predict(self, x):
         import torch

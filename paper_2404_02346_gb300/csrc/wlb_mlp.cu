@@ -99,7 +99,58 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// Inputs are mapped to [-1, 1] by the training box before the BF16 rounding.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float normalise_input(float x, float lo, float hi) {
+    return 2.0f * (x - lo) / (hi - lo) - 1.0f;
+}
+
+__device__ __forceinline__ float rcp_approx(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float v) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// GELU(z) = z Phi(z), with Phi from the rational-times-exponential form of
+// Abramowitz & Stegun 7.1.26 (|error in erf| <= 1.5e-7): for x = |z| / sqrt 2
+// and t = 1 / (1 + p x), q = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2) / 2
+// equals Phi(-|z|), so Phi(z) = q for z < 0 and 1 - q otherwise (no
+// cancellation on the negative side, no branch).  Every operation is an
+// explicit rounded intrinsic, so all kernels evaluate the same bits.
+constexpr float kAS_p = 0.3275911f, kAS_a1 = 0.254829592f, kAS_a2 = -0.284496736f, kAS_a3 = 1.421413741f,
+                kAS_a4 = -1.453152027f, kAS_a5 = 1.061405429f;
+__device__ __forceinline__ float gelu(float z) {
+    const float x = __fmul_rn(fabsf(z), 0.70710678118654752f);
+    const float t = rcp_approx(__fmaf_rn(kAS_p, x, 1.0f));
+    float p = __fmaf_rn(kAS_a5, t, kAS_a4);
+    p = __fmaf_rn(p, t, kAS_a3);
+    p = __fmaf_rn(p, t, kAS_a2);
+    p = __fmaf_rn(p, t, kAS_a1);
+    p = __fmul_rn(p, t);
+    const float e = ex2_approx(__fmul_rn(__fmul_rn(x, x), -1.4426950408889634f));  // exp(-x^2)
+    const float q = __fmul_rn(__fmul_rn(0.5f, p), e);
+    return __fmul_rn(z, z < 0.0f ? q : __fsub_rn(1.0f, q));
+}
 __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
@@ -201,7 +252,7 @@ __global__ void __launch_bounds__(128, 1) umma_gemm(Gemm g) {
                 if (MODE == 0) {
                     if (m < g.m_valid && n < g.n_valid) g.C[(size_t)m * g.ldc + n] = v[e];
                 } else if (MODE == 1) {
-                    const float z = v[e] + g.bias[n];
+                    const float z = __fadd_rn(v[e], g.bias[n]);
                     if (g.Z) g.Z[(size_t)m * g.N + n] = z;
                     const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
                     g.H[(size_t)m * g.N + n] = h;
@@ -224,6 +275,285 @@ __global__ void __launch_bounds__(128, 1) umma_gemm(Gemm g) {
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// ---------------------------------------------------------------- fused forward
+// Inference in one persistent kernel.  A CTA takes 128-row tiles in turn and
+// keeps everything between the inputs and the output on the chip: the
+// activation of the current layer is the A operand in shared memory (128 x 256
+// BF16 in the canonical K-major layout, core matrix (i, j) at i * 4096 + j * 128),
+// the accumulator lives in tensor memory, and the weights stream from L2
+// through a ring of 8 KB slots in the order the products consume them: W1
+// (256 x 16) in one slot, W2 and W3 as sixteen K = 16 slices of 256 rows each,
+// and the 16-row padded W4 (all sixteen K steps, 512 bytes apiece) in one slot.
+// Warp 8 issues the bulk copies, one lane of warp 9 the products, warps 0-7
+// the epilogues (two warps per quarter of the TMEM lanes, one per column
+// half); the epilogue warps hand each A operand to the product lane through
+// an mbarrier, and every wait is bounded (WLB_ERR_TIMEOUT, then the kernel
+// drains its copies and products and frees the tensor memory).
+// Products, epilogue arithmetic and BF16 roundings are those of the
+// layer-by-layer path, so the two give the same bits.
+constexpr int kSlots = 5, kSlotBytes = 8192, kChunks = 34;
+constexpr int kActBytes = kTileM * kHid * 2;
+constexpr int kFusedSmem = kActBytes + kSlots * kSlotBytes + 1024;
+constexpr int kEpiThreads = 256, kProducerWarp = 8, kMmaWarp = 9, kFusedThreads = 320;
+
+struct Fused {
+    const float *x;
+    long long n;
+    float *y;
+    unsigned char *inside;   // optional
+    const float *lo, *hi;
+    const float *w;          // FP32 masters: biases at ob1, ob2, ob3, ob4
+    const uint8_t *stream;   // kChunks x kSlotBytes, written by pack_stream
+    long long tiles;
+    int *err;
+};
+
+__device__ __forceinline__ void mbar_expect(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+
+// Bounded wait that also gives up once another role has raised `abort`.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t phase, volatile int *abort) {
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try(mbar, phase)) return true;
+        if ((i & 255) == 255 && *abort) return false;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 2) mlp_forward_fused(Fused a) {
+    extern __shared__ uint8_t fused_raw[];
+    uint8_t *act = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(fused_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *ring = act + kActBytes;
+    __shared__ float s_bias[3][kHid];
+    __shared__ uint64_t full[kSlots], empty[kSlots], accum, act_ready, drain;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort_store;
+    volatile int *s_abort = &s_abort_store;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long my_tiles = blockIdx.x < a.tiles ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    for (int i = tid; i < 3 * kHid; i += kFusedThreads) {
+        const int l = i / kHid;
+        s_bias[l][i % kHid] = a.w[(l == 0 ? ob1 : l == 1 ? ob2 : ob3) + i % kHid];
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kSlots; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[s])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[s])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&accum)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&act_ready)), "r"(kEpiThreads));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&drain)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_abort = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == kProducerWarp) {
+        // the weight slices of every tile, in consumption order
+        if (lane == 0) {
+            const long long total = my_tiles * kChunks;
+            long long c = 0;
+            for (; c < total; ++c) {
+                const int slot = (int)(c % kSlots);
+                const long long round = c / kSlots;
+                if (round > 0 && !mbar_wait_or_abort(&empty[slot], (uint32_t)((round - 1) & 1), s_abort)) {
+                    if (!*s_abort) {
+                        *s_abort = 1;
+                        atomicExch(a.err, 1);
+                    }
+                    break;
+                }
+                mbar_expect(&full[slot], kSlotBytes);
+                bulk_load(ring + slot * kSlotBytes, a.stream + (size_t)(c % kChunks) * kSlotBytes, kSlotBytes,
+                          &full[slot]);
+            }
+            if (c < total) {
+                // stopped early: the copies already issued land before the CTA exits
+                for (int slot = 0; slot < kSlots; ++slot) {
+                    const long long k = c > slot ? (c - slot + kSlots - 1) / kSlots : 0;
+                    if (k > 0) mbar_wait(&full[slot], (uint32_t)((k - 1) & 1));
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        // products: per layer, once the epilogue warps have written its A operand
+        if (lane == 0) {
+            const uint32_t id_hid = mma_idesc(kTileM, kHid), id_out = mma_idesc(kTileM, kOutPad);
+            long long c = 0;
+            uint32_t ready_phase = 0;
+            bool ok = true;
+            for (long long t = 0; t < my_tiles && ok; ++t) {
+                for (int layer = 0; layer < 4 && ok; ++layer) {
+                    ok = mbar_wait_or_abort(&act_ready, ready_phase, s_abort);
+                    ready_phase ^= 1;
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int slices = layer == 0 || layer == 3 ? 1 : kHid / 16;
+                    for (int s = 0; s < slices; ++s, ++c) {
+                        const int slot = (int)(c % kSlots);
+                        if (!mbar_wait_or_abort(&full[slot], (uint32_t)((c / kSlots) & 1), s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t b = smem_addr(ring + slot * kSlotBytes);
+                        if (layer < 3) {
+                            mma_bf16(tmem, smem_desc(smem_addr(act + s * 256), 128, 4096), smem_desc(b, 128, 256),
+                                     id_hid, s > 0 ? 1 : 0);
+                        } else {
+                            for (int k = 0; k < kHid / 16; ++k)
+                                mma_bf16(tmem, smem_desc(smem_addr(act + k * 256), 128, 4096),
+                                         smem_desc(b + k * 512, 128, 256), id_out, k > 0 ? 1 : 0);
+                        }
+                        mma_commit(&empty[slot]);
+                    }
+                    if (ok) mma_commit(&accum);
+                }
+            }
+            if (!ok && !*s_abort) {
+                *s_abort = 1;
+                atomicExch(a.err, 1);
+            }
+            // no product may still be running when the tensor memory is freed
+            mma_commit(&drain);
+            mbar_wait(&drain, 0);
+        }
+        __syncwarp();
+    } else {
+        // epilogue warps: two per quarter of the TMEM lanes, one per column half
+        const int q = warp & 3, col0 = (warp >> 2) * (kHid / 2);
+        const int row = 32 * q + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+        const float b4 = a.w[ob4];
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (long long t = 0; t < my_tiles && ok; ++t) {
+            const long long m0 = (blockIdx.x + t * (long long)gridDim.x) * kTileM;
+            {
+                // normalised inputs: K = 16 columns, 4 of them real
+                const int r = tid & (kTileM - 1), j = tid >> 7;
+                uint32_t pk[4] = {0, 0, 0, 0};
+                if (j == 0 && m0 + r < a.n) {
+                    const float *xr = a.x + (m0 + r) * kIn;
+                    for (int e = 0; e < kIn; e += 2) {
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(normalise_input(xr[e], a.lo[e], a.hi[e]));
+                        const __nv_bfloat16 h1 =
+                            __float2bfloat16_rn(normalise_input(xr[e + 1], a.lo[e + 1], a.hi[e + 1]));
+                        pk[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    }
+                }
+                *reinterpret_cast<uint4 *>(act + (r >> 3) * 4096 + j * 128 + (r & 7) * 16) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&act_ready);
+            for (int layer = 0; layer < 4; ++layer) {
+                ok = mbar_wait_or_abort(&accum, acc_phase, s_abort);
+                acc_phase ^= 1;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (layer < 3) {
+                    // bias + GELU -> BF16 -> the next layer's A operand
+                    const float *bias = s_bias[layer];
+                    for (int cb = 0; cb < kHid / 2 / 32; ++cb) {
+                        const int n0 = col0 + 32 * cb;
+                        float v[32];
+                        tmem_ld32(trow + (uint32_t)n0, v);
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int e = 0; e < 32; e += 2) {
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(gelu(__fadd_rn(v[e], bias[n0 + e])));
+                            const __nv_bfloat16 h1 =
+                                __float2bfloat16_rn(gelu(__fadd_rn(v[e + 1], bias[n0 + e + 1])));
+                            pk[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                        }
+                        uint8_t *dst = act + (row >> 3) * 4096 + (n0 >> 3) * 128 + (row & 7) * 16;
+#pragma unroll
+                        for (int g = 0; g < 4; ++g)
+                            *reinterpret_cast<uint4 *>(dst + 128 * g) =
+                                make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(&act_ready);
+                } else if (col0 == 0) {
+                    float v[16];
+                    tmem_ld16(trow, v);
+                    const long long i = m0 + row;
+                    if (i < a.n) {
+                        a.y[i] = v[0] + b4;
+                        if (a.inside) {
+                            bool in = true;
+                            for (int e = 0; e < kIn; ++e) {
+                                const float xv = a.x[i * kIn + e];
+                                in &= xv >= a.lo[e] && xv <= a.hi[e];
+                            }
+                            a.inside[i] = in ? 1 : 0;
+                        }
+                    }
+                }
+            }
+        }
+        if (!ok && !*s_abort) {
+            *s_abort = 1;
+            atomicExch(a.err, 1);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+// The weight stream of the fused forward (BF16, layout as described above).
+__global__ void pack_stream(const float *__restrict__ w, __nv_bfloat16 *__restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int per = kSlotBytes / 2;
+    if (e >= kChunks * per) return;
+    const int c = e / per, ob = 2 * (e % per);
+    float v = 0.0f;
+    if (c < kChunks - 1) {
+        // element (n, k) of a 256 x 16 slice at (n/8) 256 + (k/8) 128 + (n%8) 16 + (k%8) 2
+        const int n = 8 * (ob / 256) + (ob % 128) / 16, k = 8 * ((ob % 256) / 128) + (ob % 16) / 2;
+        if (c == 0)
+            v = k < kIn ? w[oW1 + n * kIn + k] : 0.0f;
+        else
+            v = w[(c <= 16 ? oW2 : oW3) + n * kHid + 16 * ((c - 1) % 16) + k];
+    } else {
+        // W4 padded to 16 rows, K step s at 512 s
+        const int r = 8 * ((ob % 512) / 256) + (ob % 128) / 16;
+        const int k = 16 * (ob / 512) + 8 * ((ob % 256) / 128) + (ob % 16) / 2;
+        v = r == 0 ? w[oW4 + k] : 0.0f;
+    }
+    out[e] = __float2bfloat16_rn(v);
+}
+
 // ---------------------------------------------------------------- small kernels
 // Inputs x (n x 4 FP32, optionally gathered through perm) -> normalised to
 // [-1, 1] by the box [lo, hi], BF16 [B][16] and [16][B] (padding zero).
@@ -235,7 +565,7 @@ __global__ void prep_inputs(const float *__restrict__ x, const float *__restrict
     const long long src = perm ? perm[first + i] : first + i;
     for (int a = 0; a < kInPad; ++a) {
         float v = 0.0f;
-        if (i < n && a < kIn) v = 2.0f * (x[src * kIn + a] - lo[a]) / (hi[a] - lo[a]) - 1.0f;
+        if (i < n && a < kIn) v = normalise_input(x[src * kIn + a], lo[a], hi[a]);
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         X0[(size_t)i * kInPad + a] = h;
         X0T[(size_t)a * Bp + i] = h;
@@ -334,6 +664,10 @@ struct wlb_mlp {
     __nv_bfloat16 *W1, *W2, *W3, *W4, *W2T, *W3T, *W4T;
     __nv_bfloat16 *X0, *X0T, *H[3], *HT[3], *dZ[3], *dZT[3], *dZ4, *dZ4T;
     float *Z[3], *Y;
+    uint8_t *Wstream = nullptr;  // fused-forward weight stream (kChunks x kSlotBytes)
+    bool stream_stale = true;    // weights changed since the stream was packed
+    bool fused = true;           // predict through mlp_forward_fused
+    int fused_grid = 0;          // CTAs of the fused forward (SMs x resident CTAs)
     int *err = nullptr, *perm = nullptr;
     long long perm_cap = 0;
     float host_lo[4], host_hi[4];
@@ -451,8 +785,42 @@ cudaError_t stage(wlb_mlp *m, const float *x, const float *t, const int *perm, l
 }
 
 cudaError_t repack(wlb_mlp *m) {
+    m->stream_stale = true;
     pack_weights<<<(kHid * kHid + 255) / 256, 256, 0, m->stream>>>(m->w, m->W1, m->W2, m->W3, m->W4, m->W2T,
                                                                    m->W3T, m->W4T);
+    return cudaGetLastError();
+}
+
+// Whole inference in one launch of the fused kernel (n >= 1).
+cudaError_t forward_fused(wlb_mlp *m, const float *x, long long n, float *y, unsigned char *inside) {
+    cudaError_t e;
+    if (m->stream_stale) {
+        pack_stream<<<(kChunks * kSlotBytes / 2 + 255) / 256, 256, 0, m->stream>>>(
+            m->w, reinterpret_cast<__nv_bfloat16 *>(m->Wstream));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        m->stream_stale = false;
+    }
+    if (m->fused_grid == 0) {
+        // the attribute applies to the current device, set for every handle
+        if ((e = cudaFuncSetAttribute(mlp_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kFusedSmem)) != cudaSuccess)
+            return e;
+        int sms = 0, per_sm = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_forward_fused, kFusedThreads,
+                                                                kFusedSmem)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        m->fused_grid = sms * per_sm;
+    }
+    Fused f{};
+    f.x = x; f.n = n; f.y = y; f.inside = inside;
+    f.lo = m->lo; f.hi = m->hi; f.w = m->w;
+    f.stream = m->Wstream;
+    f.tiles = (n + kTileM - 1) / kTileM;
+    f.err = m->err;
+    const long long grid = f.tiles < m->fused_grid ? f.tiles : m->fused_grid;
+    mlp_forward_fused<<<(unsigned)grid, kFusedThreads, kFusedSmem, m->stream>>>(f);
     return cudaGetLastError();
 }
 
@@ -502,6 +870,7 @@ wlb_status wlb_mlp_create(int batch_max, const float x_lo[4], const float x_hi[4
         oZ[l] = take(4 * B * H);
     }
     const size_t odZ4 = take(2 * B * kOutPad), odZ4T = take(2 * B * kOutPad), oY = take(4 * B * kOutPad);
+    const size_t oWs = take((size_t)kChunks * kSlotBytes);
     cudaError_t e = cudaGetDevice(&m->device);
     if (e == cudaSuccess) e = cudaMalloc(&m->mem, off);
     if (e != cudaSuccess) {
@@ -523,6 +892,7 @@ wlb_status wlb_mlp_create(int batch_max, const float x_lo[4], const float x_hi[4
         m->Z[l] = (float *)(p + oZ[l]);
     }
     m->dZ4 = (__nv_bfloat16 *)(p + odZ4); m->dZ4T = (__nv_bfloat16 *)(p + odZ4T); m->Y = (float *)(p + oY);
+    m->Wstream = (uint8_t *)(p + oWs);
     e = cudaMemsetAsync(m->mem, 0, off, m->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->lo, x_lo, 16, cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->hi, x_hi, 16, cudaMemcpyHostToDevice, m->stream);
@@ -628,7 +998,11 @@ wlb_status wlb_mlp_train(wlb_mlp *m, const float *x, const float *t, long long n
 }
 
 wlb_status wlb_mlp_predict(wlb_mlp *m, const float *x, long long n, float *y, unsigned char *inside) {
-    if (!m || !x || !y || n < 0) return WLB_ERR_ARG;
+    if (!m || n < 0 || (n > 0 && (!x || !y))) return WLB_ERR_ARG;
+    if (m->fused) {
+        if (n > 0) MLP_CUDA(m, forward_fused(m, x, n, y, inside), "fused forward");
+        return check_err(m);
+    }
     for (long long first = 0; first < n; first += m->batch_max) {
         const int cnt = (int)((n - first) < m->batch_max ? (n - first) : m->batch_max);
         const int Bp = ((cnt + kTileM - 1) / kTileM) * kTileM;
@@ -639,6 +1013,12 @@ wlb_status wlb_mlp_predict(wlb_mlp *m, const float *x, long long n, float *y, un
         MLP_CUDA(m, cudaGetLastError(), "predict head");
     }
     return check_err(m);
+}
+
+wlb_status wlb_mlp_set_fused(wlb_mlp *m, int fused) {
+    if (!m || (fused != 0 && fused != 1)) return WLB_ERR_ARG;
+    m->fused = fused == 1;
+    return WLB_OK;
 }
 
 const char *wlb_mlp_last_error(const wlb_mlp *m) { return m ? m->msg : ""; }

@@ -55,6 +55,47 @@ def test_forward_matches_oracle(wlb):
     net.close()
 
 
+def test_fused_forward_bit_identical_to_layer_by_layer(wlb):
+    """The one-launch fused forward (activations kept on the chip, weights
+    streamed) against the layer-by-layer GEMM launches: the same products,
+    epilogues and roundings, hence the same bits.  One query, a ragged single
+    tile, several tiles per CTA with a ragged end, queries outside the box,
+    again after training changed the weights (the stream is repacked), and
+    n = 0."""
+    import torch
+    net = wlb.MLP(LO, HI, batch_max=4096)
+    net.init_weights(11)
+
+    def both(x):
+        xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+        net.set_fused(True)
+        yf, inf = net.predict(xt)
+        net.set_fused(False)
+        yl, inl = net.predict(xt)
+        net.set_fused(True)
+        return yf, inf, yl, inl
+
+    for n, seed in [(1, 5), (1000, 1), (300_001, 2)]:
+        x = _inputs(n, seed)
+        x[3::7, 0] = 5.0
+        x[5::11, 3] = 0.1
+        yf, inf, yl, inl = both(x)
+        assert torch.equal(yf, yl), (n, (yf - yl).abs().max().item())
+        assert torch.equal(inf, inl), n
+        assert torch.isfinite(yf).all()
+    x = _inputs(4096, 8)
+    t = torch.tensor(np.sin(2 * x[:, 1]), dtype=torch.float32, device="cuda")
+    y0, _, _, _ = both(x)
+    net.train(torch.tensor(x, dtype=torch.float32, device="cuda"), t, epochs=2, batch=512, lr=2e-3, lr_final=1e-3)
+    yf, inf, yl, inl = both(x)
+    assert torch.equal(yf, yl) and torch.equal(inf, inl)
+    assert not torch.equal(yf, y0)
+    y, ins = net.predict(torch.empty((0, 4), dtype=torch.float32, device="cuda"))
+    assert y.numel() == 0 and ins.numel() == 0
+    assert wlb.lib().wlb_mlp_set_fused(net._h, 2) == wlb.WLB_ERR_ARG
+    net.close()
+
+
 def test_gradients_match_oracle(wlb):
     """Loss and gradients of a 384-sample batch (three 128-row tiles) against
     FP64 backpropagation with the same BF16 weights and inputs; the GPU keeps
