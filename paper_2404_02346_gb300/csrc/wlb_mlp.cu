@@ -134,22 +134,22 @@ __device__ __forceinline__ float ex2_approx(float v) {
 // GELU(z) = z Phi(z), with Phi from the rational-times-exponential form of
 // Abramowitz & Stegun 7.1.26 (|error in erf| <= 1.5e-7): for x = |z| / sqrt 2
 // and t = 1 / (1 + p x), q = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2) / 2
-// equals Phi(-|z|), so Phi(z) = q for z < 0 and 1 - q otherwise (no
-// cancellation on the negative side, no branch).  Every operation is an
-// explicit rounded intrinsic, so all kernels evaluate the same bits.
+// equals Phi(-|z|), and z Phi(z) = z / 2 + |z| (1/2 - q) for either sign (no
+// branch).  The halving is folded into the coefficients (exact in binary).
+// Every operation is an explicit rounded intrinsic, so all kernels evaluate
+// the same bits.
 constexpr float kAS_p = 0.3275911f, kAS_a1 = 0.254829592f, kAS_a2 = -0.284496736f, kAS_a3 = 1.421413741f,
                 kAS_a4 = -1.453152027f, kAS_a5 = 1.061405429f;
 __device__ __forceinline__ float gelu(float z) {
-    const float x = __fmul_rn(fabsf(z), 0.70710678118654752f);
-    const float t = rcp_approx(__fmaf_rn(kAS_p, x, 1.0f));
-    float p = __fmaf_rn(kAS_a5, t, kAS_a4);
-    p = __fmaf_rn(p, t, kAS_a3);
-    p = __fmaf_rn(p, t, kAS_a2);
-    p = __fmaf_rn(p, t, kAS_a1);
+    const float az = fabsf(z);
+    const float t = rcp_approx(__fmaf_rn(kAS_p * 0.70710678118654752f, az, 1.0f));
+    float p = __fmaf_rn(0.5f * kAS_a5, t, 0.5f * kAS_a4);
+    p = __fmaf_rn(p, t, 0.5f * kAS_a3);
+    p = __fmaf_rn(p, t, 0.5f * kAS_a2);
+    p = __fmaf_rn(p, t, 0.5f * kAS_a1);
     p = __fmul_rn(p, t);
-    const float e = ex2_approx(__fmul_rn(__fmul_rn(x, x), -1.4426950408889634f));  // exp(-x^2)
-    const float q = __fmul_rn(__fmul_rn(0.5f, p), e);
-    return __fmul_rn(z, z < 0.0f ? q : __fsub_rn(1.0f, q));
+    const float e = ex2_approx(__fmul_rn(__fmul_rn(z, z), -0.72134752044448170f));  // exp(-z^2 / 2)
+    return __fmaf_rn(az, __fsub_rn(0.5f, __fmul_rn(p, e)), __fmul_rn(0.5f, z));
 }
 __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
@@ -486,10 +486,9 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_forward_fused(Fused a) {
                         uint32_t pk[16];
 #pragma unroll
                         for (int e = 0; e < 32; e += 2) {
-                            const __nv_bfloat16 h0 = __float2bfloat16_rn(gelu(__fadd_rn(v[e], bias[n0 + e])));
-                            const __nv_bfloat16 h1 =
-                                __float2bfloat16_rn(gelu(__fadd_rn(v[e + 1], bias[n0 + e + 1])));
-                            pk[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(gelu(__fadd_rn(v[e], bias[n0 + e])),
+                                                                           gelu(__fadd_rn(v[e + 1], bias[n0 + e + 1])));
+                            pk[e / 2] = *reinterpret_cast<const uint32_t *>(&h);
                         }
                         uint8_t *dst = act + (row >> 3) * 4096 + (n0 >> 3) * 128 + (row & 7) * 16;
 #pragma unroll
@@ -805,13 +804,30 @@ cudaError_t forward_fused(wlb_mlp *m, const float *x, long long n, float *y, uns
         if ((e = cudaFuncSetAttribute(mlp_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       kFusedSmem)) != cudaSuccess)
             return e;
-        int sms = 0, per_sm = 0;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_forward_fused, kFusedThreads,
-                                                                kFusedSmem)) != cudaSuccess)
+        // two CTAs per SM need the largest shared-memory carveout
+        if ((e = cudaFuncSetAttribute(mlp_forward_fused, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
             return e;
+        // resident CTAs per SM from the SM's shared memory and registers, at
+        // most two (each holds half of the tensor memory)
+        int sms = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
+        cudaFuncAttributes fa{};
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device)) !=
+                cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, m->device)) !=
+                cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, m->device)) !=
+                cudaSuccess ||
+            (e = cudaFuncGetAttributes(&fa, mlp_forward_fused)) != cudaSuccess)
+            return e;
+        const long long smem_block = (long long)fa.sharedSizeBytes + kFusedSmem + reserved;
+        const long long regs_block = (long long)fa.numRegs * kFusedThreads;
+        long long per_sm = 2;
+        if (smem_sm / smem_block < per_sm) per_sm = smem_sm / smem_block;
+        if (regs_block > 0 && regs_sm / regs_block < per_sm) per_sm = regs_sm / regs_block;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        m->fused_grid = sms * per_sm;
+        m->fused_grid = (int)(sms * per_sm);
     }
     Fused f{};
     f.x = x; f.n = n; f.y = y; f.inside = inside;
