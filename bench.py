@@ -406,6 +406,62 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_predict(sur, q, args):
+    """Seconds per predict call (host clock) and the roofline of the fused
+    forward (CUDA events on the current stream; each call is one kernel
+    launch plus a 4-byte status read)."""
+    import torch
+
+    for _ in range(args.warmup):
+        sur.predict(q)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        ev[2 * s].record()
+        sur.predict(q)
+        ev[2 * s + 1].record()
+    torch.cuda.synchronize()
+    q_s = (time.perf_counter() - t0) / args.steps
+    k_s = sum(ev[2 * s].elapsed_time(ev[2 * s + 1]) for s in range(args.steps)) / args.steps * 1e-3
+    # algorithmic products: 2 (4*256 + 2*256*256 + 256) flops per query
+    flops = 2.0 * (4 * 256 + 2 * 256 * 256 + 256) * int(q.shape[0])
+    peaks = _peaks()
+    peak = peaks.get("bf16_tflops") if peaks else None
+    achieved = flops / k_s / 1e12
+    return q_s, {"bound": "tensor", "kernel": "mlp_forward_fused", "achieved": achieved, "peak": peak,
+                 "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+                 "peak_source": "measured bf16_tflops (burst)" if peak else None, "kernel_ms": k_s * 1e3}
+
+
+def run_surrogate_infer(args):
+    """Inference of the surrogate network alone: the fused tensor-core forward
+    on seeded queries with seeded initial weights (trained weights do the same
+    work)."""
+    import numpy as np
+    import torch
+
+    from paper_2404_02346_gb300 import build as B
+    from paper_2404_02346_gb300 import surrogate as S
+
+    B.build()
+    sur = S.Surrogate(workloads.SURROGATE_BOX)
+    sur.net.init_weights(args.seed)
+    q = torch.tensor(np.array(workloads.surrogate_queries(args.queries, seed=args.seed + 2000), dtype=np.float32),
+                     device="cuda")
+    q_s, roofline = _time_predict(sur, q, args)
+    sur.close()
+    line = {
+        "metric": "radiation forces/s, learned surrogate (inference)", "value": args.queries / q_s,
+        "unit": "forces/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": q_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 weights/activations, fp32 accumulate (tcgen05)", "data": "synthetic",
+        "config": {"workload": "MLP 4-256-256-256-1 GELU, seeded initial weights; %d seeded queries" % args.queries},
+        "roofline": roofline, "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_surrogate(args):
     """Learned surrogate: 20k training and 2k held-out forces from the batched
     2D lattice runs (512-lattice chunks of 192^2 D2Q5, 25 periods), training on
@@ -432,40 +488,20 @@ def run_surrogate(args):
     y, _ = sur.predict([p["features"] for p in val])
     err = y.cpu().numpy() - t_val
     scale = float(np.abs(t_val).max())
-    q = torch.tensor(np.array(workloads.surrogate_queries(1 << 20, seed=args.seed + 2000), dtype=np.float32),
+    q = torch.tensor(np.array(workloads.surrogate_queries(args.queries, seed=args.seed + 2000), dtype=np.float32),
                      device="cuda")
-    for _ in range(args.warmup):
-        sur.predict(q)
-    torch.cuda.synchronize()
-    # each call: one fused-forward launch plus a 4-byte status read, on the current stream
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
-    t0 = time.perf_counter()
-    for s in range(args.steps):
-        ev[2 * s].record()
-        sur.predict(q)
-        ev[2 * s + 1].record()
-    torch.cuda.synchronize()
-    q_s = (time.perf_counter() - t0) / args.steps
-    k_s = sum(ev[2 * s].elapsed_time(ev[2 * s + 1]) for s in range(args.steps)) / args.steps * 1e-3
+    q_s, roofline = _time_predict(sur, q, args)
     sur.close()
-    # algorithmic products: 2 (4*256 + 2*256*256 + 256) flops per query
-    flops = 2.0 * (4 * 256 + 2 * 256 * 256 + 256) * (1 << 20)
-    peaks = _peaks()
-    peak = peaks.get("bf16_tflops") if peaks else None
-    achieved = flops / k_s / 1e12
     lb_rate = (len(train) + len(val)) / lb_s
     line = {
-        "metric": "radiation forces/s, learned surrogate", "value": (1 << 20) / q_s, "unit": "forces/s",
+        "metric": "radiation forces/s, learned surrogate", "value": args.queries / q_s, "unit": "forces/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": q_s * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 weights/activations, fp32 accumulate (tcgen05)", "data": "synthetic",
         "config": {"workload": "MLP 4-256-256-256-1 GELU; 20k train / 2k held-out 2D lattice forces "
-                               "(192^2 D2Q5, 25 periods); 1M seeded queries",
+                               "(192^2 D2Q5, 25 periods); %d seeded queries" % args.queries,
                    "epochs": args.epochs, "batch": 512},
-        "roofline": {"bound": "tensor", "kernel": "mlp_forward_fused", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
-                     "traffic": None, "peak_source": "measured bf16_tflops (burst)" if peak else None,
-                     "kernel_ms": k_s * 1e3},
+        "roofline": roofline,
         "gpu_launches": args.steps,
         "lattice_forces_per_s_batched": lb_rate,
         "speedup_vs_batched_lattice": (1 << 20) / q_s / lb_rate,
@@ -574,15 +610,19 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"],
                     help="population storage (the benchmark workload is FP32)")
     ap.add_argument("--workload", default="sphere256",
-                    choices=["sphere256", "ensemble3d", "ensemble2d", "surrogate", "sweep512"],
-                    help="sphere256: the benchmark line; ensembles: batched forces/s; surrogate: learned model")
+                    choices=["sphere256", "ensemble3d", "ensemble2d", "surrogate", "surrogate_infer", "sweep512"],
+                    help="sphere256: the benchmark line; ensembles: batched forces/s; surrogate: learned model "
+                         "(surrogate_infer: its inference alone)")
     ap.add_argument("--epochs", type=int, default=1500, help="surrogate training epochs")
+    ap.add_argument("--queries", type=int, default=1 << 20, help="surrogate inference queries")
     args = ap.parse_args()
     prob = workloads.sphere_3d(seed=args.seed, precision=args.precision)
     if args.profile:
         run_profile(args, prob)
     elif args.workload == "surrogate":
         run_surrogate(args)
+    elif args.workload == "surrogate_infer":
+        run_surrogate_infer(args)
     elif args.workload == "sweep512":
         run_sweep(args)
     elif args.workload != "sphere256":

@@ -335,6 +335,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t phas
     return false;
 }
 
+
 __global__ void __launch_bounds__(kFusedThreads, 2) mlp_forward_fused(Fused a) {
     extern __shared__ uint8_t fused_raw[];
     uint8_t *act = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(fused_raw) + 1023) & ~(uintptr_t)1023);
@@ -374,12 +375,14 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_forward_fused(Fused a) {
     if (warp == kProducerWarp) {
         // the weight slices of every tile, in consumption order
         if (lane == 0) {
+            const uint8_t *src = a.stream;
             const long long total = my_tiles * kChunks;
+            // 32-bit counters advanced by increment: the loop is on the critical path
+            int slot = 0, chunk = 0;
+            uint32_t round_par = 0;  // parity of c / kSlots
             long long c = 0;
             for (; c < total; ++c) {
-                const int slot = (int)(c % kSlots);
-                const long long round = c / kSlots;
-                if (round > 0 && !mbar_wait_or_abort(&empty[slot], (uint32_t)((round - 1) & 1), s_abort)) {
+                if (c >= kSlots && !mbar_wait_or_abort(&empty[slot], round_par ^ 1u, s_abort)) {
                     if (!*s_abort) {
                         *s_abort = 1;
                         atomicExch(a.err, 1);
@@ -387,8 +390,12 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_forward_fused(Fused a) {
                     break;
                 }
                 mbar_expect(&full[slot], kSlotBytes);
-                bulk_load(ring + slot * kSlotBytes, a.stream + (size_t)(c % kChunks) * kSlotBytes, kSlotBytes,
-                          &full[slot]);
+                bulk_load(ring + slot * kSlotBytes, src + chunk * kSlotBytes, kSlotBytes, &full[slot]);
+                if (++chunk == kChunks) chunk = 0;
+                if (++slot == kSlots) {
+                    slot = 0;
+                    round_par ^= 1u;
+                }
             }
             if (c < total) {
                 // stopped early: the copies already issued land before the CTA exits
@@ -403,7 +410,12 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_forward_fused(Fused a) {
         // products: per layer, once the epilogue warps have written its A operand
         if (lane == 0) {
             const uint32_t id_hid = mma_idesc(kTileM, kHid), id_out = mma_idesc(kTileM, kOutPad);
-            long long c = 0;
+            // descriptors: the start-address field (bits 0-13, address / 16) takes
+            // the offsets directly (every address is below 256 KB)
+            const uint64_t a_desc = smem_desc(smem_addr(act), 128, 4096);
+            const uint64_t b_desc = smem_desc(smem_addr(ring), 128, 256);
+            int slot = 0;
+            uint32_t full_par = 0;  // parity of c / kSlots
             uint32_t ready_phase = 0;
             bool ok = true;
             for (long long t = 0; t < my_tiles && ok; ++t) {
@@ -413,22 +425,24 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_forward_fused(Fused a) {
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const int slices = layer == 0 || layer == 3 ? 1 : kHid / 16;
-                    for (int s = 0; s < slices; ++s, ++c) {
-                        const int slot = (int)(c % kSlots);
-                        if (!mbar_wait_or_abort(&full[slot], (uint32_t)((c / kSlots) & 1), s_abort)) {
+                    for (int s = 0; s < slices; ++s) {
+                        if (!mbar_wait_or_abort(&full[slot], full_par, s_abort)) {
                             ok = false;
                             break;
                         }
-                        const uint32_t b = smem_addr(ring + slot * kSlotBytes);
+                        const uint64_t b = b_desc + (uint64_t)(slot * (kSlotBytes >> 4));
                         if (layer < 3) {
-                            mma_bf16(tmem, smem_desc(smem_addr(act + s * 256), 128, 4096), smem_desc(b, 128, 256),
-                                     id_hid, s > 0 ? 1 : 0);
+                            mma_bf16(tmem, a_desc + (uint64_t)(s * (256 >> 4)), b, id_hid, s > 0 ? 1 : 0);
                         } else {
                             for (int k = 0; k < kHid / 16; ++k)
-                                mma_bf16(tmem, smem_desc(smem_addr(act + k * 256), 128, 4096),
-                                         smem_desc(b + k * 512, 128, 256), id_out, k > 0 ? 1 : 0);
+                                mma_bf16(tmem, a_desc + (uint64_t)(k * (256 >> 4)), b + (uint64_t)(k * (512 >> 4)),
+                                         id_out, k > 0 ? 1 : 0);
                         }
                         mma_commit(&empty[slot]);
+                        if (++slot == kSlots) {
+                            slot = 0;
+                            full_par ^= 1u;
+                        }
                     }
                     if (ok) mma_commit(&accum);
                 }
