@@ -338,6 +338,7 @@ def run_ensemble(args):
     """Batched ensemble: forces/s of one batched launch sequence over all
     lattices, against the same lattices run one at a time through the
     single-lattice path (a sample of them, timed on the same GPU)."""
+    import numpy as np
     import torch
 
     import paper_2404_02346_gb300 as wlb
@@ -389,6 +390,25 @@ def run_ensemble(args):
         s.close()
     ax = probs[0]["wave_axis"]
     rel = max(abs(F[i, ax] - singles[k][ax]) / max(abs(singles[k][ax]), 1e-300) for k, i in enumerate(idx))
+    # roofline of the batched update: algorithmic bytes of one launch over every
+    # lattice (each population read and written once per launch, plus the class
+    # byte) / its duration, from the library's own event timing of update-only
+    # steps (autotune: all lattices before their windows; the sampling launch
+    # between updates exits at once)
+    q = 2 * probs[0]["dim"] + 1
+    size = {"f32": 4, "f16": 2, "f64": 8}[args.precision]
+    bpu = 2 * q * size + 1
+    cells_all = sum(int(np.prod(p["n"][:p["dim"]])) for p in probs)
+    spl = info.steps_per_launch if info.steps_per_launch > 0 else 1
+    launch_ms = tune["ms_per_step"] * spl
+    achieved = bpu * cells_all / (launch_ms * 1e-3) / 1e9
+    peaks = _peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": ("batched two-step update" if spl == 2 else "batched update")
+                                          + " (%s storage), all lattices" % args.precision,
+                "bytes_per_cell_per_launch": bpu, "avg_launch_us": launch_ms * 1e3,
+                "peak_source": ("measured" if peaks and "hbm_gbs" in peaks else "fallback") + " hbm_gbs"}
     line = {
         "metric": "radiation forces/s, batched ensemble", "value": len(probs) / (ms * 1e-3), "unit": "forces/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -401,6 +421,7 @@ def run_ensemble(args):
                             "glups": lu_single / (ms_single * 1e-3) / 1e9,
                             "max_rel_force_diff_vs_batch": rel},
         "speedup_vs_single": (len(probs) / (ms * 1e-3)) / (len(idx) / (ms_single * 1e-3)),
+        "roofline": roofline,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -134,8 +134,8 @@ typedef struct {
                                    4, 8 or 2                                   */
     int vector_path;            /* 1 if the row-vectorised update kernel is used */
     int steps_per_launch;       /* steps per update launch: 1, or 2 with
-                                   wlb_set_two_step (the default where it
-                                   applies)                                     */
+                                   wlb_set_two_step (the default for 3D
+                                   lattices where it applies)                   */
     int two_step_rows;          /* slab height of the two-step kernel, 0 off    */
     int two_step_segments;      /* warps per lattice row in it, 0 off           */
 } wlb_info;
@@ -379,8 +379,11 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
  * and at least one slab row fitting the shared memory (nx up to about 1500
  * FP32 cells).
  * 2D lattices (periodic, any storage, rows of at most two 16-byte chunks
- * per lane and 8 values per lane) take it too: each warp sweeps a chunk of
- * rows, both steps in its registers (slab_rows must be 0).
+ * per lane and 8 values per lane) take it on request (off by default: a
+ * single lattice of such short rows has too few row chunks to fill the SMs
+ * and one step per launch is faster; 2D batches use it by default): each
+ * warp sweeps a chunk of rows, both steps in its registers (slab_rows must
+ * be 0).
  * Elsewhere, or with enable = 0, every step is one launch.  enable: 0 off;
  * 1 on, lane layout chosen by the library; 2 on with one 16-byte chunk per
  * lane (more, lighter warps); 3 on with two (WLB_ERR_ARG if unsupported).

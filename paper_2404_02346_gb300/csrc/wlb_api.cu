@@ -311,8 +311,10 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
         wlb_destroy(h);
         return WLB_ERR_CUDA;
     }
-    // steps two per launch wherever the kernel applies (bit-identical)
-    {
+    // steps two per launch by default on 3D lattices where the kernel applies
+    // (bit-identical); a single 2D lattice has too few row chunks to fill the
+    // SMs, and one step per launch is faster there
+    if (h->g.dim == 3) {
         cudaError_t pe = cudaSuccess;
         if (two_step_plan(h, 0, 1, &h->two_plan, &pe) && pe == cudaSuccess) h->two_step = true;
     }

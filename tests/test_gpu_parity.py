@@ -398,10 +398,13 @@ def test_two_step_is_bit_identical(wlb, shape, lam, precision, rows, cpl, segmen
     ((64, 32), 16.0, "f32"),     # short lattice: 4-row chunks
 ])
 def test_two_step_2d_is_bit_identical(wlb, shape, lam, precision):
-    """2D row sweep (two steps per launch, default) against one step per
-    launch: forces and fields equal bit for bit; odd tail of direct steps."""
+    """2D row sweep (two steps per launch, on request) against one step per
+    launch (the 2D default): forces and fields equal bit for bit; odd tail of
+    direct steps."""
     prob = workloads.problem(2, shape, 1, lam, 4.0, (shape[0] / 2 + 0.25, lam / 8), cp=0.32, n_surface=64,
                              n_periods=5, n_avg_periods=2)
+    with wlb.Solver(prob, precision=precision) as s:
+        assert s.info().steps_per_launch == 1
     out = []
     for enable in (True, False):
         with wlb.Solver(prob, precision=precision) as s:
