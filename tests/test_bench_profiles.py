@@ -1,0 +1,30 @@
+"""bench.py reports the update kernel's DRAM traffic from the committed ncu
+summaries only when they were taken on the current kernel source.  These
+checks fail when a kernel changes without a new capture, and check the lookup
+itself (a foreign source hash gives no traffic)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+CELLS = 256 ** 3
+
+
+@pytest.mark.parametrize("steps_per_launch", [1, 2])
+def test_committed_profile_matches_current_kernel(steps_per_launch):
+    traffic = bench._traffic(bench._kernel_sha(steps_per_launch), steps_per_launch)
+    assert traffic is not None, "kernel source changed since its profile was captured"
+    # every population read and written once per launch, plus the class byte:
+    # the measured bytes lie within a few per cent of 57 B per cell
+    algorithmic = 57.0 * CELLS
+    assert 0.9 * algorithmic < traffic < 1.1 * algorithmic
+
+
+def test_foreign_source_hash_gives_no_traffic():
+    assert bench._traffic("0" * 64, 2) is None
+    assert bench._traffic("0" * 64, 1) is None
