@@ -203,6 +203,31 @@ wlb_status wlb_surface(wlb_handle *h, double *pts_out);
  * of Eq. (79) is +-1 in double precision.  Synchronises. */
 wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out);
 
+/* Checkpoint and resume.  The paper has no counterpart: a long run can stop
+ * and continue in another handle or process.  The state after wlb_init and
+ * any steps is the current populations, the running surface sums of the
+ * current period, the folded FP64 sums, the non-finite flag and the step
+ * counters; everything else follows from the parameters and is rebuilt by
+ * the setup.  The buffer is host memory owned by the caller: a 256-byte
+ * header (format tag, version, the parameters as doubles, the counters and
+ * array sizes), then the arrays in that order, each padded to 8 bytes.
+ *
+ *   wlb_state_bytes  *bytes: the buffer size the two calls below need.
+ *   wlb_save_state   waits for the handle's stream, then copies the state
+ *                    into host[0 .. wlb_state_bytes).  WLB_ERR_STATE before
+ *                    wlb_init; WLB_ERR_ARG if bytes is too small.
+ *   wlb_load_state   restores a state written by wlb_save_state for a handle
+ *                    with the same parameters (runs the setup first if the
+ *                    handle has not been initialised).  Steps issued after it
+ *                    continue exactly where the saved handle stopped: forces
+ *                    and fields are bit-identical.  WLB_ERR_ARG for a short
+ *                    buffer, a foreign format or version, other parameters,
+ *                    or counters out of range (nothing is changed then).
+ * Both synchronise. */
+wlb_status wlb_state_bytes(const wlb_handle *h, size_t *bytes);
+wlb_status wlb_save_state(wlb_handle *h, void *host, size_t bytes);
+wlb_status wlb_load_state(wlb_handle *h, const void *host, size_t bytes);
+
 /*
  * Allocation-free averaging (the paper has no counterpart of this call).
  *

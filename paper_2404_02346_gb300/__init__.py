@@ -90,6 +90,9 @@ _SIGNATURES = {
     "wlb_fields": (ctypes.c_int, [_VP, _DP, _DP]),
     "wlb_surface": (ctypes.c_int, [_VP, _DP]),
     "wlb_mask": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ubyte)]),
+    "wlb_state_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    "wlb_save_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    "wlb_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "wlb_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(Info)]),
     "wlb_set_two_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "wlb_destroy": (ctypes.c_int, [_VP]),
@@ -271,6 +274,21 @@ class Solver:
         _check(lib().wlb_mask(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))), self._h,
                "wlb_mask")
         return m
+
+    def save_state(self):
+        """Checkpoint (wlb_save_state) as a numpy uint8 array."""
+        n = ctypes.c_size_t()
+        _check(lib().wlb_state_bytes(self._h, ctypes.byref(n)), self._h, "wlb_state_bytes")
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(lib().wlb_save_state(self._h, ctypes.c_void_p(buf.ctypes.data), n.value), self._h,
+               "wlb_save_state")
+        return buf
+
+    def load_state(self, buf):
+        """Resume from a checkpoint written by save_state (wlb_load_state)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().wlb_load_state(self._h, ctypes.c_void_p(buf.ctypes.data), buf.size), self._h,
+               "wlb_load_state")
 
 
 def compute_force(problem, precision=None):
