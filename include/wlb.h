@@ -206,11 +206,12 @@ wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out);
 /* Checkpoint and resume.  The paper has no counterpart: a long run can stop
  * and continue in another handle or process.  The state after wlb_init and
  * any steps is the current populations, the running surface sums of the
- * current period, the folded FP64 sums, the non-finite flag and the step
- * counters; everything else follows from the parameters and is rebuilt by
- * the setup.  The buffer is host memory owned by the caller: a 256-byte
- * header (format tag, version, the parameters as doubles, the counters and
- * array sizes), then the arrays in that order, each padded to 8 bytes.
+ * current period, the folded FP64 sums, the force history, the non-finite
+ * flag and the step counters; everything else follows from the parameters
+ * and is rebuilt by the setup.  The buffer is host memory owned by the
+ * caller: a fixed-size header (format tag, version, the parameters as
+ * doubles, the counters and array sizes), then the arrays in that order,
+ * each padded to 8 bytes.
  *
  *   wlb_state_bytes  *bytes: the buffer size the two calls below need.
  *   wlb_save_state   waits for the handle's stream, then copies the state
@@ -227,6 +228,18 @@ wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out);
 wlb_status wlb_state_bytes(const wlb_handle *h, size_t *bytes);
 wlb_status wlb_save_state(wlb_handle *h, void *host, size_t bytes);
 wlb_status wlb_load_state(wlb_handle *h, const void *host, size_t bytes);
+
+/* Force history (Sec. VII follows the force over time to see it settle).
+ * After the fold of every full sampled period the force numerator of the FP64
+ * sums folded so far is recorded on the device (graph replays included), up
+ * to n_periods entries since wlb_init (later ones are counted, not kept).
+ * out: host, max_periods x 3 doubles: the force of each recorded period in
+ * order, Eq. (14) over that period's T samples alone; with whole sampled
+ * periods their mean is the wlb_force result.  A partial period that
+ * wlb_force folds is not recorded.  *count: periods recorded (may exceed
+ * max_periods; only min(count, max_periods, n_periods) rows are written).
+ * WLB_ERR_STATE before wlb_init.  Synchronises. */
+wlb_status wlb_force_history(wlb_handle *h, double *out, int max_periods, int *count);
 
 /*
  * Allocation-free averaging (the paper has no counterpart of this call).

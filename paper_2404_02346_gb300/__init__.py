@@ -91,6 +91,8 @@ _SIGNATURES = {
     "wlb_surface": (ctypes.c_int, [_VP, _DP]),
     "wlb_mask": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ubyte)]),
     "wlb_state_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    "wlb_force_history": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]),
     "wlb_save_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "wlb_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "wlb_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(Info)]),
@@ -274,6 +276,15 @@ class Solver:
         _check(lib().wlb_mask(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))), self._h,
                "wlb_mask")
         return m
+
+    def force_history(self):
+        """Force of every recorded full sampled period, (count, 3) (wlb_force_history)."""
+        cap = max(int(self.params.n_periods), 1)
+        out = np.zeros((cap, 3))
+        n = ctypes.c_int()
+        _check(lib().wlb_force_history(self._h, out.ctypes.data_as(_DP), cap, ctypes.byref(n)), self._h,
+               "wlb_force_history")
+        return out[: min(n.value, cap)]
 
     def save_state(self):
         """Checkpoint (wlb_save_state) as a numpy uint8 array."""

@@ -76,6 +76,7 @@ Geometry make_geometry(const wlb_params *p) {
     g.wall_damping = p->wall_damping;
     g.source_amplitude = p->source_amplitude;
     g.period = (long long)std::nearbyint(p->wavelength / p->c0);
+    g.n_periods = p->n_periods;
     g.n_surface = p->n_surface;
     g.stencil = g.dim == 3 ? 27 : 9;
     return g;
@@ -111,6 +112,9 @@ size_t layout(const Geometry &g, Prec prec, char *base, Buffers *b) {
     t.acc = take(N * 5 * T);
     t.acc64 = (double *)take(N * 5 * sizeof(double));
     t.force = (double *)take(4 * sizeof(double));
+    t.hist = (double *)take((size_t)(g.n_periods > 1 ? g.n_periods : 1) * 4 * sizeof(double));
+    t.hist_tmp = (double *)take(4 * sizeof(double));
+    t.hist_n = (unsigned long long *)take(sizeof(unsigned long long));
     t.err = (int *)take(sizeof(int));
     t.ptab = (double *)take(sizeof(double) * g.n[g.wave_axis]);
     t.stage_cells = g.ncell < kStageCells ? g.ncell : kStageCells;
@@ -173,7 +177,10 @@ cudaError_t issue_period(wlb_handle *h, int start, bool sampled, cudaStream_t s)
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
-    if (sampled) return wlb::launch_fold(h->g, h->b, h->prec, s);
+    if (sampled) {
+        cudaError_t e = wlb::launch_fold(h->g, h->b, h->prec, s);
+        return e != cudaSuccess ? e : wlb::launch_record_period(h->g, h->b, s);
+    }
     return cudaSuccess;
 }
 
@@ -327,6 +334,7 @@ wlb_status wlb_init(wlb_handle *h) {
     if (!h) return WLB_ERR_ARG;
     DeviceGuard dg(h->device);
     WLB_CUDA(h, wlb::launch_setup(h->g, h->b, h->prec, h->stream), "setup kernels");
+    WLB_CUDA(h, cudaMemsetAsync(h->b.hist_n, 0, sizeof(unsigned long long), h->stream), "history reset");
     h->src = 0;
     h->steps_done = h->samples_done = h->samples_in_period = 0;
     h->initialised = true;
@@ -362,6 +370,7 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
                 h->samples_in_period += 2;
                 if (h->samples_in_period == h->period) {
                     WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->prec, h->stream), "fold kernel");
+                    WLB_CUDA(h, wlb::launch_record_period(h->g, h->b, h->stream), "history kernels");
                     h->samples_in_period = 0;
                 }
             }
@@ -375,6 +384,7 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
             h->samples_done += 1;
             if (++h->samples_in_period == h->period) {
                 WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->prec, h->stream), "fold kernel");
+                WLB_CUDA(h, wlb::launch_record_period(h->g, h->b, h->stream), "history kernels");
                 h->samples_in_period = 0;
             }
         }

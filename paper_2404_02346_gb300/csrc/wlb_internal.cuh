@@ -32,6 +32,7 @@ struct Geometry {
     int driven;            // 1: driven walls along wave_axis (Sec. VII)
     double wall_damping, source_amplitude;
     long long period;      // T = lambda / c0 steps
+    int n_periods;         // run length in periods (sizes the force history)
     int n_surface;
     int stencil;           // 3^dim
 };
@@ -49,6 +50,10 @@ struct Buffers {
     void *acc;             // n_surface * 5 reals: running sums within a period
     double *acc64;         // n_surface * 5: folded sums
     double *force;         // 4 doubles
+    double *hist;          // max(n_periods, 1) x 4: force numerator of the sums folded after each
+                           // full sampled period (Eq. 14 with 1 / N_w = 1)
+    double *hist_tmp;      // 4 doubles: the entry being recorded
+    unsigned long long *hist_n;  // entries recorded (may exceed the capacity; the excess is dropped)
     int *err;              // 1 int: non-finite accumulator seen
     double *ptab;          // n[wave_axis]: incident pressure along the wave axis (setup)
     double *stage;         // stage_cells * (1 + dim): field read-back staging
@@ -67,6 +72,9 @@ cudaError_t launch_step(const Geometry &g, const Buffers &b, Prec p, int src, bo
                         cudaStream_t s);
 cudaError_t launch_fold(const Geometry &g, const Buffers &b, Prec p, cudaStream_t s);
 cudaError_t launch_force(const Geometry &g, const Buffers &b, double n_window, cudaStream_t s);
+// After the fold of a full sampled period: append the force numerator of the
+// folded sums to the history (wlb_history.cu).
+cudaError_t launch_record_period(const Geometry &g, const Buffers &b, cudaStream_t s);
 cudaError_t launch_fields(const Geometry &g, const Buffers &b, Prec p, int src,
                           long long first_cell, long long count, cudaStream_t s);
 bool update_is_vectorised(const Geometry &g, Prec p);

@@ -1,9 +1,10 @@
 // Checkpoint and resume of a handle's dynamic state (C ABI, include/wlb.h).
 // Not part of the paper's method: a long run can stop and continue.  After
 // wlb_init and any steps the state is the current population buffer, the
-// running surface sums of the current period, the folded FP64 sums, the error
-// flag and the step counters.  Everything else (classes, c^2, surface points,
-// stencils) is a function of the parameters and is rebuilt by the setup.
+// running surface sums of the current period, the folded FP64 sums, the force
+// history, the error flag and the step counters.  Everything else (classes,
+// c^2, surface points, stencils) is a function of the parameters and is
+// rebuilt by the setup.
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -24,7 +25,7 @@ struct Header {
     uint32_t version, header_bytes;
     double params[kParamWords];
     long long steps_done, samples_done, samples_in_period;
-    unsigned long long pop_bytes, acc_bytes, acc64_bytes;
+    unsigned long long pop_bytes, acc_bytes, acc64_bytes, hist_bytes;
 };
 
 void canonical(const wlb_params &p, double (&w)[kParamWords]) {
@@ -38,7 +39,7 @@ void canonical(const wlb_params &p, double (&w)[kParamWords]) {
 }
 
 struct Sizes {
-    size_t pop, acc, acc64, total;
+    size_t pop, acc, acc64, hist, total;
 };
 
 // Array sizes and the offsets that follow from them (each 8-byte aligned).
@@ -48,8 +49,9 @@ Sizes sizes_of(const wlb_handle *h) {
     s.pop = (size_t)h->g.q * nc * wlb::pop_bytes(h->prec);
     s.acc = N * 5 * wlb::real_bytes(h->prec);
     s.acc64 = N * 5 * sizeof(double);
+    s.hist = (size_t)(h->g.n_periods > 1 ? h->g.n_periods : 1) * 4 * sizeof(double);
     auto up8 = [](size_t v) { return (v + 7) & ~(size_t)7; };
-    s.total = sizeof(Header) + up8(s.pop) + up8(s.acc) + s.acc64 + 8;  // + error flag
+    s.total = sizeof(Header) + up8(s.pop) + up8(s.acc) + s.acc64 + s.hist + 8 + 8;  // + count, error flag
     return s;
 }
 
@@ -100,13 +102,15 @@ wlb_status wlb_save_state(wlb_handle *h, void *host, size_t bytes) {
     hd.pop_bytes = s.pop;
     hd.acc_bytes = s.acc;
     hd.acc64_bytes = s.acc64;
+    hd.hist_bytes = s.hist;
     char *out = static_cast<char *>(host);
     memcpy(out, &hd, sizeof(hd));
     size_t off = sizeof(Header);
     struct Part {
         const void *src;
         size_t n;
-    } parts[4] = {{h->b.pop[h->src], s.pop}, {h->b.acc, s.acc}, {h->b.acc64, s.acc64}, {h->b.err, sizeof(int)}};
+    } parts[6] = {{h->b.pop[h->src], s.pop}, {h->b.acc, s.acc},           {h->b.acc64, s.acc64},
+                  {h->b.hist, s.hist},         {h->b.hist_n, 8},           {h->b.err, sizeof(int)}};
     for (const Part &p : parts) {
         if (p.n) {
             cudaError_t e = cudaMemcpyAsync(out + off, p.src, p.n, cudaMemcpyDeviceToHost, h->stream);
@@ -130,7 +134,7 @@ wlb_status wlb_load_state(wlb_handle *h, const void *host, size_t bytes) {
     double mine[kParamWords];
     canonical(h->p, mine);
     if (memcmp(mine, hd.params, sizeof(mine)) != 0 || hd.pop_bytes != s.pop || hd.acc_bytes != s.acc ||
-        hd.acc64_bytes != s.acc64)
+        hd.acc64_bytes != s.acc64 || hd.hist_bytes != s.hist)
         return sfail(h, WLB_ERR_ARG, "state was saved for other parameters");
     if (hd.steps_done < 0 || hd.samples_done < 0 || hd.samples_in_period < 0 ||
         hd.samples_in_period >= h->period)
@@ -145,7 +149,8 @@ wlb_status wlb_load_state(wlb_handle *h, const void *host, size_t bytes) {
     struct Part {
         void *dst;
         size_t n;
-    } parts[4] = {{h->b.pop[0], s.pop}, {h->b.acc, s.acc}, {h->b.acc64, s.acc64}, {h->b.err, sizeof(int)}};
+    } parts[6] = {{h->b.pop[0], s.pop}, {h->b.acc, s.acc},      {h->b.acc64, s.acc64},
+                  {h->b.hist, s.hist},  {h->b.hist_n, 8},       {h->b.err, sizeof(int)}};
     for (const Part &p : parts) {
         if (p.n) {
             cudaError_t e = cudaMemcpyAsync(p.dst, in + off, p.n, cudaMemcpyHostToDevice, h->stream);

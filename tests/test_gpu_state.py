@@ -62,7 +62,8 @@ def test_resume_is_bit_identical(wlb, case):
                 states[i] = s.save_state()
         F = s.force()
         p1, u1 = s.fields()
-    assert np.any(F != 0)
+        hist = s.force_history()
+    assert np.any(F != 0) and len(hist) == prob["n_window"] // prob["period"]
     for cut, state in states.items():
         with wlb.Solver(prob) as r:  # never initialised: the load runs the setup
             r.load_state(state)
@@ -72,6 +73,7 @@ def test_resume_is_bit_identical(wlb, case):
             assert np.array_equal(r.force(), F), (case, cut)
             q1, v1 = r.fields()
             assert np.array_equal(q1, p1) and np.array_equal(v1, u1), (case, cut)
+            assert np.array_equal(r.force_history(), hist), (case, cut)
 
 
 def test_state_is_checked(wlb):
