@@ -301,8 +301,9 @@ def run_gpu(args, prob):
         peak, peak_src = 6800.0, "fallback"
     traffic = _traffic(_kernel_sha(spl), spl) if args.precision == "f32" else None
     # per force: 3 setup kernels, one update launch per step (sampling fused into
-    # it on the row-vectorised path), one fold per averaged period, the force
-    per_step = 3 + n_window + n_free // spl + (0 if info.vector_path else n_window) + n_avg + 1
+    # it on the row-vectorised path), per averaged period a fold and the two
+    # launches that record its force in the history, the force
+    per_step = 3 + n_window + n_free // spl + (0 if info.vector_path else n_window) + 3 * n_avg + 1
     launches = args.steps * per_step
     if rank == 0:
         line = {
