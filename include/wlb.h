@@ -230,16 +230,19 @@ wlb_status wlb_save_state(wlb_handle *h, void *host, size_t bytes);
 wlb_status wlb_load_state(wlb_handle *h, const void *host, size_t bytes);
 
 /* Force history (Sec. VII follows the force over time to see it settle).
- * After the fold of every full sampled period the force numerator of the FP64
- * sums folded so far is recorded on the device (graph replays included), up
- * to n_periods entries since wlb_init (later ones are counted, not kept).
- * out: host, max_periods x 3 doubles: the force of each recorded period in
- * order, Eq. (14) over that period's T samples alone; with whole sampled
- * periods their mean is the wlb_force result.  A partial period that
- * wlb_force folds is not recorded.  *count: periods recorded (may exceed
- * max_periods; only min(count, max_periods, n_periods) rows are written).
+ * Every fold of the running surface sums is recorded on the device (graph
+ * replays included): each full sampled period, and the partial period that
+ * wlb_force folds when called inside one.  Up to n_periods + 1 entries are
+ * kept since wlb_init (later ones are counted, not kept).
+ *   out          host, max_entries x 3 doubles: per entry, Eq. (14) over the
+ *                samples that fold added alone (a sampled period's force).
+ *   samples_out  host, max_entries long longs (may be NULL): those sample
+ *                counts (T for a full period).  The mean of the rows weighted
+ *                by their counts is the wlb_force result.
+ *   *count       entries recorded (may exceed max_entries; only
+ *                min(count, max_entries, n_periods + 1) rows are written).
  * WLB_ERR_STATE before wlb_init.  Synchronises. */
-wlb_status wlb_force_history(wlb_handle *h, double *out, int max_periods, int *count);
+wlb_status wlb_force_history(wlb_handle *h, double *out, long long *samples_out, int max_entries, int *count);
 
 /*
  * Allocation-free averaging (the paper has no counterpart of this call).

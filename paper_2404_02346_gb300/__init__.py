@@ -91,7 +91,8 @@ _SIGNATURES = {
     "wlb_surface": (ctypes.c_int, [_VP, _DP]),
     "wlb_mask": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ubyte)]),
     "wlb_state_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
-    "wlb_force_history": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+    "wlb_force_history": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
     "wlb_save_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "wlb_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
@@ -277,14 +278,19 @@ class Solver:
                "wlb_mask")
         return m
 
-    def force_history(self):
-        """Force of every recorded full sampled period, (count, 3) (wlb_force_history)."""
-        cap = max(int(self.params.n_periods), 1)
+    def force_history(self, with_samples=False):
+        """Force of every recorded fold (each full sampled period, and a partial
+        one folded by force()), (count, 3); with_samples also returns the sample
+        count of each row (wlb_force_history)."""
+        cap = max(int(self.params.n_periods), 1) + 1
         out = np.zeros((cap, 3))
+        smp = np.zeros(cap, dtype=np.int64)
         n = ctypes.c_int()
-        _check(lib().wlb_force_history(self._h, out.ctypes.data_as(_DP), cap, ctypes.byref(n)), self._h,
-               "wlb_force_history")
-        return out[: min(n.value, cap)]
+        _check(lib().wlb_force_history(self._h, out.ctypes.data_as(_DP),
+                                       smp.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), cap,
+                                       ctypes.byref(n)), self._h, "wlb_force_history")
+        k = min(n.value, cap)
+        return (out[:k], smp[:k]) if with_samples else out[:k]
 
     def save_state(self):
         """Checkpoint (wlb_save_state) as a numpy uint8 array."""

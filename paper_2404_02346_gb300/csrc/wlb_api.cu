@@ -112,7 +112,7 @@ size_t layout(const Geometry &g, Prec prec, char *base, Buffers *b) {
     t.acc = take(N * 5 * T);
     t.acc64 = (double *)take(N * 5 * sizeof(double));
     t.force = (double *)take(4 * sizeof(double));
-    t.hist = (double *)take((size_t)(g.n_periods > 1 ? g.n_periods : 1) * 4 * sizeof(double));
+    t.hist = (double *)take((size_t)history_capacity(g) * 4 * sizeof(double));
     t.hist_tmp = (double *)take(4 * sizeof(double));
     t.hist_n = (unsigned long long *)take(sizeof(unsigned long long));
     t.err = (int *)take(sizeof(int));
@@ -179,7 +179,7 @@ cudaError_t issue_period(wlb_handle *h, int start, bool sampled, cudaStream_t s)
     }
     if (sampled) {
         cudaError_t e = wlb::launch_fold(h->g, h->b, h->prec, s);
-        return e != cudaSuccess ? e : wlb::launch_record_period(h->g, h->b, s);
+        return e != cudaSuccess ? e : wlb::launch_record_fold(h->g, h->b, h->period, s);
     }
     return cudaSuccess;
 }
@@ -370,7 +370,7 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
                 h->samples_in_period += 2;
                 if (h->samples_in_period == h->period) {
                     WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->prec, h->stream), "fold kernel");
-                    WLB_CUDA(h, wlb::launch_record_period(h->g, h->b, h->stream), "history kernels");
+                    WLB_CUDA(h, wlb::launch_record_fold(h->g, h->b, h->period, h->stream), "history kernels");
                     h->samples_in_period = 0;
                 }
             }
@@ -384,7 +384,7 @@ wlb_status wlb_step(wlb_handle *h, long long n, int sample) {
             h->samples_done += 1;
             if (++h->samples_in_period == h->period) {
                 WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->prec, h->stream), "fold kernel");
-                WLB_CUDA(h, wlb::launch_record_period(h->g, h->b, h->stream), "history kernels");
+                WLB_CUDA(h, wlb::launch_record_fold(h->g, h->b, h->period, h->stream), "history kernels");
                 h->samples_in_period = 0;
             }
         }
@@ -404,6 +404,7 @@ wlb_status wlb_force(wlb_handle *h, double force_out[3]) {
     }
     if (h->samples_in_period > 0) {
         WLB_CUDA(h, wlb::launch_fold(h->g, h->b, h->prec, h->stream), "fold kernel");
+        WLB_CUDA(h, wlb::launch_record_fold(h->g, h->b, h->samples_in_period, h->stream), "history kernels");
         h->samples_in_period = 0;
     }
     WLB_CUDA(h, wlb::launch_force(h->g, h->b, (double)h->samples_done, h->stream), "force kernel");

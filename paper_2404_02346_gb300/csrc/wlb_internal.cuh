@@ -50,8 +50,8 @@ struct Buffers {
     void *acc;             // n_surface * 5 reals: running sums within a period
     double *acc64;         // n_surface * 5: folded sums
     double *force;         // 4 doubles
-    double *hist;          // max(n_periods, 1) x 4: force numerator of the sums folded after each
-                           // full sampled period (Eq. 14 with 1 / N_w = 1)
+    double *hist;          // history_capacity x 4: after each fold, the force numerator of the sums
+                           // folded so far (Eq. 14 with 1 / N_w = 1) and the samples that fold added
     double *hist_tmp;      // 4 doubles: the entry being recorded
     unsigned long long *hist_n;  // entries recorded (may exceed the capacity; the excess is dropped)
     int *err;              // 1 int: non-finite accumulator seen
@@ -72,9 +72,11 @@ cudaError_t launch_step(const Geometry &g, const Buffers &b, Prec p, int src, bo
                         cudaStream_t s);
 cudaError_t launch_fold(const Geometry &g, const Buffers &b, Prec p, cudaStream_t s);
 cudaError_t launch_force(const Geometry &g, const Buffers &b, double n_window, cudaStream_t s);
-// After the fold of a full sampled period: append the force numerator of the
-// folded sums to the history (wlb_history.cu).
-cudaError_t launch_record_period(const Geometry &g, const Buffers &b, cudaStream_t s);
+// After a fold that added `samples` samples: append the force numerator of the
+// folded sums and that count to the history (wlb_history.cu).
+cudaError_t launch_record_fold(const Geometry &g, const Buffers &b, long long samples, cudaStream_t s);
+// History entries kept: every full period of the run plus one partial fold.
+inline long long history_capacity(const Geometry &g) { return (g.n_periods > 1 ? g.n_periods : 1) + 1; }
 cudaError_t launch_fields(const Geometry &g, const Buffers &b, Prec p, int src,
                           long long first_cell, long long count, cudaStream_t s);
 bool update_is_vectorised(const Geometry &g, Prec p);

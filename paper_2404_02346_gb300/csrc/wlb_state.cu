@@ -49,7 +49,7 @@ Sizes sizes_of(const wlb_handle *h) {
     s.pop = (size_t)h->g.q * nc * wlb::pop_bytes(h->prec);
     s.acc = N * 5 * wlb::real_bytes(h->prec);
     s.acc64 = N * 5 * sizeof(double);
-    s.hist = (size_t)(h->g.n_periods > 1 ? h->g.n_periods : 1) * 4 * sizeof(double);
+    s.hist = (size_t)wlb::history_capacity(h->g) * 4 * sizeof(double);
     auto up8 = [](size_t v) { return (v + 7) & ~(size_t)7; };
     s.total = sizeof(Header) + up8(s.pop) + up8(s.acc) + s.acc64 + s.hist + 8 + 8;  // + count, error flag
     return s;

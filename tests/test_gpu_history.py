@@ -1,9 +1,10 @@
-"""Force history (wlb_force_history): the force of every full sampled period.
-Pinned against the oracle without a history of its own: a run averaging the
-last k periods gives F(k), so the j-th period from the end has the force
-j F(j) - (j - 1) F(j - 1) (Eq. 14 is linear in the sums).  Also: the mean of
-the history is the run's force, a partial last period is not recorded, and
-the call is refused before wlb_init."""
+"""Force history (wlb_force_history): the force of every fold of the running
+sums (each full sampled period, and a partial one wlb_force folds).  Pinned
+against the oracle without a history of its own: a run averaging the last k
+periods gives F(k), so the j-th period from the end has the force
+j F(j) - (j - 1) F(j - 1) (Eq. 14 is linear in the sums).  Also: the
+sample-weighted mean of the history is the force, also with a partial fold in
+the middle of a run, and the call is refused before wlb_init."""
 import numpy as np
 import pytest
 
@@ -52,9 +53,16 @@ def test_history_mean_is_the_force_3d_two_step(wlb):
         assert hist.shape == (5, 3)
         scale = np.abs(F).max()
         assert np.abs(hist.mean(axis=0) - F).max() <= 1e-12 * scale
-        # a partial sampled period is not recorded
+        # partial folds (force() inside a period) are rows with their own counts
         T = prob["period"]
         s.init()
         s.step(prob["n_steps"] - prob["n_window"], sample=False)
         s.step(2 * T + 11, sample=True)
         assert len(s.force_history()) == 2
+        s.force()
+        s.step(T + 5, sample=True)
+        F2 = s.force()
+        hist, n = s.force_history(with_samples=True)
+        assert list(n) == [T, T, 11, T, 5]
+        mean = (hist * n[:, None]).sum(axis=0) / n.sum()
+        assert np.abs(mean - F2).max() <= 1e-12 * np.abs(F2).max()
