@@ -183,8 +183,20 @@ wlb_status wlb_step(wlb_handle *h, long long n_steps, int sample);
 wlb_status wlb_force(wlb_handle *h, double force_out[3]);
 
 /* The whole protocol: wlb_init, (n_periods - n_avg_periods) T unsampled steps,
- * n_avg_periods T sampled steps, wlb_force. */
+ * n_avg_periods T sampled steps, wlb_force.  With a deadline set (below) and
+ * passed: WLB_ERR_TIMEOUT (see wlb_set_deadline). */
 wlb_status wlb_run(wlb_handle *h, double force_out[3]);
+
+/* Host-clock watchdog of wlb_run (the paper has no counterpart).  seconds > 0:
+ * wlb_run then issues its steps one period at a time with at most two periods
+ * queued, and between periods compares the host clock since the call with
+ * the limit; past it, it waits for the queued periods to finish (their
+ * device work cannot be recalled) and returns WLB_ERR_TIMEOUT with the handle
+ * consistent: wlb_get_info's steps_done counts the steps that ran, and
+ * wlb_step / wlb_force / wlb_init may follow.  Results within the limit are
+ * bit-identical to a run without it.  seconds = 0 (the default) turns it off;
+ * WLB_ERR_ARG for a negative or non-finite value. */
+wlb_status wlb_set_deadline(wlb_handle *h, double seconds);
 
 /* Fields at the current time: p1 = c^2 rho1 and u1 = J1 / rho0 (Eq. 62).
  * p1_out: nx*ny*nz doubles, u1_out: dim*nx*ny*nz doubles laid out

@@ -91,6 +91,7 @@ _SIGNATURES = {
     "wlb_surface": (ctypes.c_int, [_VP, _DP]),
     "wlb_mask": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ubyte)]),
     "wlb_state_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    "wlb_set_deadline": (ctypes.c_int, [_VP, ctypes.c_double]),
     "wlb_force_history": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
@@ -249,6 +250,10 @@ class Solver:
 
     def step(self, n, sample=False):
         _check(lib().wlb_step(self._h, int(n), 1 if sample else 0), self._h, "wlb_step")
+
+    def set_deadline(self, seconds):
+        """Host-clock limit of run() (wlb_set_deadline); 0 turns it off."""
+        _check(lib().wlb_set_deadline(self._h, float(seconds)), self._h, "wlb_set_deadline")
 
     def force(self):
         F = np.zeros(3)

@@ -1,9 +1,11 @@
 // Host side of the C ABI declared in include/wlb.h: parameter validation,
 // workspace layout, the step loop (per-period CUDA graphs) and read-back.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "../../include/wlb.h"
 #include "wlb_internal.cuh"
@@ -421,13 +423,58 @@ wlb_status wlb_force(wlb_handle *h, double force_out[3]) {
     return WLB_OK;
 }
 
+// Steps of a deadline run: one period per call, at most two periods queued;
+// between them the host polls the older period's marker against its clock.
+static wlb_status steps_within(wlb_handle *h, long long n, int sample, std::chrono::steady_clock::time_point t0,
+                               long long *issued) {
+    using clk = std::chrono::steady_clock;
+    auto late = [&] { return std::chrono::duration<double>(clk::now() - t0).count() > h->deadline_s; };
+    while (n > 0) {
+        const long long chunk = n < h->period ? n : h->period;
+        wlb_status st = wlb_step(h, chunk, sample);
+        if (st != WLB_OK) return st;
+        cudaEvent_t mine = h->marks[*issued & 1], older = h->marks[(*issued + 1) & 1];
+        WLB_CUDA(h, cudaEventRecord(mine, h->stream), "period marker");
+        if (*issued > 0) {
+            cudaError_t q;
+            while ((q = cudaEventQuery(older)) == cudaErrorNotReady && !late())
+                std::this_thread::sleep_for(std::chrono::microseconds(50));
+            if (q != cudaSuccess && q != cudaErrorNotReady) return fail(h, WLB_ERR_CUDA, "period marker", q);
+        }
+        ++*issued;
+        n -= chunk;
+        if (late()) {
+            // what is queued still completes: drain it, keep the handle consistent
+            WLB_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+            return fail(h, WLB_ERR_TIMEOUT, "wlb_run deadline reached");
+        }
+    }
+    return WLB_OK;
+}
+
 wlb_status wlb_run(wlb_handle *h, double force_out[3]) {
     if (!h || !force_out) return WLB_ERR_ARG;
     wlb_status s = wlb_init(h);
-    if (s == WLB_OK) s = wlb_step(h, h->n_steps - h->n_window, 0);
-    if (s == WLB_OK) s = wlb_step(h, h->n_window, 1);
+    if (h->deadline_s > 0.0) {
+        const auto t0 = std::chrono::steady_clock::now();
+        long long issued = 0;
+        if (s == WLB_OK) s = steps_within(h, h->n_steps - h->n_window, 0, t0, &issued);
+        if (s == WLB_OK) s = steps_within(h, h->n_window, 1, t0, &issued);
+    } else {
+        if (s == WLB_OK) s = wlb_step(h, h->n_steps - h->n_window, 0);
+        if (s == WLB_OK) s = wlb_step(h, h->n_window, 1);
+    }
     if (s == WLB_OK) s = wlb_force(h, force_out);
     return s;
+}
+
+wlb_status wlb_set_deadline(wlb_handle *h, double seconds) {
+    if (!h || !(seconds >= 0.0) || !std::isfinite(seconds)) return WLB_ERR_ARG;
+    DeviceGuard dg(h->device);
+    for (int i = 0; i < 2 && seconds > 0.0; ++i)
+        if (!h->marks[i]) WLB_CUDA(h, cudaEventCreateWithFlags(&h->marks[i], cudaEventDisableTiming), "marker event");
+    h->deadline_s = seconds;
+    return WLB_OK;
 }
 
 wlb_status wlb_fields(wlb_handle *h, double *p1_out, double *u1_out) {
@@ -521,6 +568,8 @@ wlb_status wlb_destroy(wlb_handle *h) {
     if (h->side.stream) cudaStreamDestroy(h->side.stream);
     if (h->side.fork) cudaEventDestroy(h->side.fork);
     if (h->side.join) cudaEventDestroy(h->side.join);
+    for (cudaEvent_t m : h->marks)
+        if (m) cudaEventDestroy(m);
     if (h->host_out) cudaFreeHost(h->host_out);
     if (h->owned) cudaFree(h->owned);
     delete h;

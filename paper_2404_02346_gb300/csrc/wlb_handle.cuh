@@ -30,6 +30,8 @@ struct wlb_handle {
     bool two_step = false;      // unsampled steps two per launch (wlb_set_two_step)
     wlb::TwoStepPlan two_plan;  // its grid, set by wlb_set_two_step
     wlb::SideStream side;       // sampling beside the two-step update
+    double deadline_s = 0.0;    // wlb_run's host-clock limit, 0 = none (wlb_set_deadline)
+    cudaEvent_t marks[2] = {nullptr, nullptr};  // period markers of a deadline run
     char err[512] = {0};
 };
 
