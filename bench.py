@@ -157,9 +157,10 @@ def job_totals(local_ms, local_units, world, device=None):
     return float(t.item()), float(u.item())
 
 
-def cpu_baseline(prob, target_s=15.0, steps=None):
+def cpu_baseline(prob, target_s=15.0, steps=None, max_steps=60):
     """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
-    the full lattice for a few LB steps, a third of them sampled."""
+    the full lattice for a few LB steps (about target_s seconds, at most
+    max_steps), a third of them sampled."""
     import oracle
     oracle.build.build()
     if steps is None:
@@ -167,7 +168,7 @@ def cpu_baseline(prob, target_s=15.0, steps=None):
         t0 = time.perf_counter()
         oracle.run(probe)
         t_probe = time.perf_counter() - t0
-        steps = max(3, min(60, int(3 * target_s / max(t_probe, 1e-3))))
+        steps = max(3, min(max_steps, int(3 * target_s / max(t_probe, 1e-3))))
         steps -= steps % 3
     sample = dict(prob, n_steps=steps, n_window=steps // 3)
     t0 = time.perf_counter()
@@ -178,6 +179,23 @@ def cpu_baseline(prob, target_s=15.0, steps=None):
             "kind": "oracle",
             "sample": "%d LB steps (%d sampled) of the %dx%dx%d lattice incl. setup, %.1f s"
                       % (steps, steps // 3, *prob["n"], dt)}
+
+
+def cpu_baseline_mlp(sur, q, n=65536):
+    """Time the FP64 oracle network, as it stands, on a bounded sample of the
+    queries (the first n), with the surrogate's weights."""
+    import numpy as np
+
+    from oracle import mlp as ref
+    x = q[:n].cpu().numpy().astype(np.float64)
+    theta = ref.bf16(sur.net.get_weights().astype(np.float64))
+    xn = ref.bf16(ref.normalise(x, sur.lo.astype(np.float64), sur.hi.astype(np.float64)))
+    t0 = time.perf_counter()
+    ref.forward(theta, xn)
+    dt = time.perf_counter() - t0
+    return {"value": len(x) / dt, "unit": "forces/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d queries through the FP64 numpy network (BLAS threads: all host cores), %.2f s"
+                      % (len(x), dt)}
 
 
 def run_reference(args, prob):
@@ -405,6 +423,14 @@ def run_ensemble(args):
     achieved = bpu * cells_all / (launch_ms * 1e-3) / 1e9
     peaks = _peaks()
     peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
+    # the oracle on a bounded sample of the first lattice, as forces/s at the
+    # ensemble's mean lattice updates per force
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(probs[0], target_s=10.0, max_steps=30000)
+        lu_per_force = info.lattice_updates / len(probs)
+        cpu = dict(cpu, glups=cpu["value"], value=cpu["value"] * 1e9 / lu_per_force, unit="forces/s",
+                   sample=cpu["sample"] + "; forces/s at the ensemble's mean %.3g LU per force" % lu_per_force)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "kernel": ("batched two-step update" if spl == 2 else "batched update")
                                           + " (%s storage), all lattices" % args.precision,
@@ -423,6 +449,7 @@ def run_ensemble(args):
                             "max_rel_force_diff_vs_batch": rel},
         "speedup_vs_single": (len(probs) / (ms * 1e-3)) / (len(idx) / (ms_single * 1e-3)),
         "roofline": roofline,
+        "cpu_baseline": cpu,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -472,6 +499,7 @@ def run_surrogate_infer(args):
     q = torch.tensor(np.array(workloads.surrogate_queries(args.queries, seed=args.seed + 2000), dtype=np.float32),
                      device="cuda")
     q_s, roofline = _time_predict(sur, q, args)
+    cpu = None if args.no_cpu_baseline else cpu_baseline_mlp(sur, q)
     sur.close()
     line = {
         "metric": "radiation forces/s, learned surrogate (inference)", "value": args.queries / q_s,
@@ -479,7 +507,7 @@ def run_surrogate_infer(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 weights/activations, fp32 accumulate (tcgen05)", "data": "synthetic",
         "config": {"workload": "MLP 4-256-256-256-1 GELU, seeded initial weights; %d seeded queries" % args.queries},
-        "roofline": roofline, "gpu_launches": args.steps,
+        "roofline": roofline, "gpu_launches": args.steps, "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
 
@@ -513,6 +541,7 @@ def run_surrogate(args):
     q = torch.tensor(np.array(workloads.surrogate_queries(args.queries, seed=args.seed + 2000), dtype=np.float32),
                      device="cuda")
     q_s, roofline = _time_predict(sur, q, args)
+    cpu = None if args.no_cpu_baseline else cpu_baseline_mlp(sur, q)
     sur.close()
     lb_rate = (len(train) + len(val)) / lb_s
     line = {
@@ -525,6 +554,7 @@ def run_surrogate(args):
                    "epochs": args.epochs, "batch": 512},
         "roofline": roofline,
         "gpu_launches": args.steps,
+        "cpu_baseline": cpu,
         "lattice_forces_per_s_batched": lb_rate,
         "speedup_vs_batched_lattice": (1 << 20) / q_s / lb_rate,
         "train_s": train_s, "final_train_loss": float(hist[-1]),
