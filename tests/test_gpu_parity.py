@@ -113,25 +113,29 @@ def _mem_available_gb():
     return 0.0
 
 
-def test_sphere_512_full_size_short_run(wlb):
+@pytest.mark.parametrize("precision,force_rtol", [("f32", 1e-4), ("f16", 1e-2)])
+def test_sphere_512_full_size_short_run(wlb, precision, force_rtol):
     """The 512^3 sweep lattice (R = 24, 4096 points, a position with a large
-    force) in the launch configuration the sweep times (two steps per launch,
-    rows of two warps), for 8 steps with 4 sampled: classes and points
-    bit-exact, force within tolerance of the oracle."""
+    force) in the launch configuration the sweep times (two steps per launch),
+    for 8 steps with 4 sampled, per stored precision: classes and points
+    bit-exact, force within tolerance of the FP64 oracle (FP16 storage: the
+    1 % bound of the other FP16 cases)."""
     if _mem_available_gb() < 48:
         pytest.skip("the FP64 oracle of a 512^3 lattice needs about 16 GB of host memory")
-    prob = workloads.sphere_3d_large(position=4)
+    prob = workloads.sphere_3d_large(position=4, precision=precision)
     short = dict(prob, n_steps=8, n_window=4)
     o = oracle.run(short)
     with wlb.Solver(prob) as s:
         info = s.info()
-        assert info.steps_per_launch == 2 and info.two_step_segments == 2
+        assert info.steps_per_launch == 2
+        if precision == "f32":
+            assert info.two_step_segments == 2
         s.init()
         s.step(4, sample=False)
         s.step(4, sample=True)
         F = s.force()
         g = {"force": F, "mask": s.mask(), "points": s.surface()}
-    _compare(short, g, o, p1_tol=None, force_rtol=1e-4)
+    _compare(short, g, o, p1_tol=None, force_rtol=force_rtol)
 
 
 def test_sphere_256_full_length_uniform_medium_closed_form(wlb):
