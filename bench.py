@@ -580,16 +580,40 @@ def run_sweep(args):
     B.build()
     stream = torch.cuda.Stream()
     precs = ["f32", "f16"] if args.precision == "f32" else [args.precision]
+    positions = list(range(16))[: max(1, min(16, args.positions))]
     res = {}
     lu = 0
     t_all = {}
+    cells = 512 ** 3
+    peaks = _peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
+    roofline = {}
+    for prec in precs:
+        # the update kernel alone: 64 unsampled steps of position 0, CUDA events
+        with wlb.Solver(workloads.sphere_3d_large(position=0, precision=prec), stream=stream) as s0:
+            info = s0.info()
+            s0.init()
+            s0.step(64)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s0.step(64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            launch_ms = a.elapsed_time(b) / 64 * info.steps_per_launch
+            achieved = info.bytes_per_update * cells / (launch_ms * 1e-3) / 1e9
+            roofline[prec] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                              "frac": achieved / peak, "traffic": None,
+                              "kernel": "update2_slab, %d steps/launch, %d-row slabs (%s storage)"
+                                        % (info.steps_per_launch, info.two_step_rows, prec),
+                              "bytes_per_cell_per_launch": info.bytes_per_update,
+                              "avg_launch_us": launch_ms * 1e3}
     for prec in precs:
         forces = []
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
-        cells = 512 ** 3
         start.record(stream)
-        for j in range(16):
+        for j in positions:
             prob = workloads.sphere_3d_large(position=j, precision=prec)
             with wlb.Solver(prob, stream=stream) as sj:
                 forces.append(float(sj.run()[2]))
@@ -598,10 +622,10 @@ def run_sweep(args):
         torch.cuda.synchronize()
         t_all[prec] = start.elapsed_time(end) * 1e-3
         res[prec] = forces
-        lu = cells * steps * 16
+        lu = cells * steps * len(positions)
     f32 = res.get("f32")
     fit = None
-    if f32:
+    if f32 and len(f32) == 16:
         amp = max(abs(v) for v in f32)
         kz = [j * math.pi / 15 for j in range(16)]
         # least-squares amplitude of the sin(2 k z0) law and the residual
@@ -612,7 +636,9 @@ def run_sweep(args):
         "metric": "512^3 force-vs-position sweep", "value": lu / t_all[precs[0]] / 1e9, "unit": "GLUPS",
         "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": t_all[precs[0]] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precs[0], "data": "synthetic",
-        "config": {"workload": "512^3 D3Q7, lambda=256, R=24, 4096 points, kappa~=0.5, 16 positions x 30 periods"},
+        "config": {"workload": "512^3 D3Q7, lambda=256, R=24, 4096 points, kappa~=0.5, %d of the 16 positions "
+                               "x 30 periods" % len(positions)},
+        "roofline": roofline[precs[0]], "roofline_by_precision": roofline,
         "forces": res, "sin2kz_fit_f32": fit,
         "seconds": t_all,
         "glups": {p: lu / t_all[p] / 1e9 for p in precs},
@@ -667,6 +693,7 @@ def main():
                          "(surrogate_infer: its inference alone)")
     ap.add_argument("--epochs", type=int, default=1500, help="surrogate training epochs")
     ap.add_argument("--queries", type=int, default=1 << 20, help="surrogate inference queries")
+    ap.add_argument("--positions", type=int, default=16, help="sweep512: the first N of the 16 positions")
     args = ap.parse_args()
     prob = workloads.sphere_3d(seed=args.seed, precision=args.precision)
     if args.profile:
