@@ -639,6 +639,8 @@ def run_sweep(args):
         "config": {"workload": "512^3 D3Q7, lambda=256, R=24, 4096 points, kappa~=0.5, %d of the 16 positions "
                                "x 30 periods" % len(positions)},
         "roofline": roofline[precs[0]], "roofline_by_precision": roofline,
+        "cpu_baseline": (None if args.no_cpu_baseline
+                         else cpu_baseline(workloads.sphere_3d_large(position=0), steps=6)),
         "forces": res, "sin2kz_fit_f32": fit,
         "seconds": t_all,
         "glups": {p: lu / t_all[p] / 1e9 for p in precs},
