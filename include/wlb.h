@@ -29,7 +29,8 @@
  *     with cudaMalloc in wlb_create and frees in wlb_destroy.
  *   - Work is issued asynchronously on the CUDA stream given to wlb_create;
  *     calls that return host data (wlb_force, wlb_fields, wlb_surface,
- *     wlb_mask, wlb_run) synchronise that stream before returning.
+ *     wlb_mask, wlb_run, wlb_force_history, wlb_save_state) and
+ *     wlb_load_state synchronise that stream before returning.
  *   - A handle is not thread safe; distinct handles are independent.
  *   - Population layout in device memory: structure of arrays f[i][z][y][x],
  *     x fastest, velocity order i = 0 (rest), +x, -x, +y, -y, +z, -z.
@@ -50,7 +51,8 @@ typedef enum {
     WLB_ERR_CUDA = 3,      /* a CUDA runtime call or kernel launch failed       */
     WLB_ERR_OOM = 4,       /* device or host allocation failed, or workspace too small */
     WLB_ERR_STATE = 5,     /* call out of order (e.g. wlb_step before wlb_init) */
-    WLB_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up (reported, never a hang) */
+    WLB_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up (reported, never a hang),
+                              or wlb_run's host-clock deadline passed            */
 } wlb_status;
 
 typedef enum { WLB_D2Q5 = 0, WLB_D3Q7 = 1 } wlb_lattice;          /* Fig. 8   */
