@@ -164,7 +164,8 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
 /* Setup and initial condition (asynchronous): cell classes and sound-speed
  * field (Eq. 79), surface elements and interpolation weights (Sec. VI,
  * Eqs. 80-82), the standing wave imposed through the equilibrium (Eq. 72),
- * and zeroed time averages.  Resets the step and sample counters. */
+ * and zeroed time averages.  Resets the step and sample counters and the
+ * force history. */
 wlb_status wlb_init(wlb_handle *h);
 
 /* Advance n_steps >= 0 lattice steps (asynchronous).  Each step streams and
