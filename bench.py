@@ -1,21 +1,27 @@
 """Benchmark: wave-LB GLUPS and radiation forces/s on one GB300.
 
-One step = one whole force evaluation of the 3D sphere workload (256^3 D3Q7,
-FP32 populations, lambda = 128, R = 16 at lambda/8, seeded compressibility
-ratio, 2000 Fibonacci points, 30 periods = 15360 LB steps, last 10 averaged):
-setup and initial condition, the unsampled and the sampled periods, and the
-FP64 force, all on the device.  Inputs (two population copies of 470 MB each)
-are far larger than L2, so no flush is needed between steps.
+Default line (--workload sphere512): the 512^3 force-vs-position workload of
+Sec. VII (F proportional to sin 2kz): 512^3 D3Q7, FP32 populations,
+lambda = 256, R = 24, kappa~ = 0.5, 4096 Fibonacci points, 30 periods (30720
+LB steps) with the last 10 averaged.  One step = the whole force evaluation
+of one position k z0 = j pi / 15 (setup and initial condition, the unsampled
+and the sampled periods, the FP64 force, all on the device); step i takes
+position j = i mod 16, so 16 steps cover the sweep.  --workload sphere256 is
+the 256^3 sphere (lambda = 128, R = 16 at lambda/8, seeded compressibility
+ratio, 2000 points, 15360 steps).  Inputs (two population copies of 3.8 GB at
+512^3, 470 MB at 256^3) are far larger than L2, so no flush is needed.
 
 value       GLUPS = cells x LB steps / device time (CUDA events on the
             library's stream, max over ranks), whole job.
 roofline    the update kernel: algorithmic bytes per launch (57 B per cell:
             7 + 7 FP32 populations and the class byte) / its average launch
-            time, measured over the unsampled periods of the timed steps.
+            time, measured over the unsampled periods of the timed steps;
+            glups_bound is the GLUPS that one pass over the state per launch
+            at the measured copy bandwidth allows.
 e2e         the same metric through the public C ABI from host parameters to
             host force: handle creation on a torch workspace, wlb_run, read-back.
 cpu_baseline  the FP64 oracle on the host cores, a bounded sample of the same
-            lattice (a few LB steps with sampling), as GLUPS.
+            lattice (a few LB steps with sampling, setup included), as GLUPS.
 
 --impl reference times the oracle alone (the paper has no code to run).
 N > 1 (torchrun): independent replicas, one lattice per rank ("replicas only").
@@ -34,7 +40,11 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 
-WORKLOAD = "3D sphere 256^3 D3Q7 FP32, lambda=128, R=16 at lambda/8, 2000 Fibonacci points, 30 periods avg last 10"
+WORKLOADS = {
+    "sphere512": "3D sphere 512^3 D3Q7 FP32 force-vs-position sweep, lambda=256, R=24, kappa~=0.5, 4096 Fibonacci "
+                 "points, 30 periods avg last 10; step i = position k z0 = (i mod 16) pi/15",
+    "sphere256": "3D sphere 256^3 D3Q7 FP32, lambda=128, R=16 at lambda/8, 2000 Fibonacci points, 30 periods avg last 10",
+}
 METRIC = "wave-LB GLUPS (% HBM roofline); radiation forces/s at <=1% err vs FP64 oracle"
 
 
@@ -54,11 +64,16 @@ def _peaks():
         return None
 
 
-def _traffic(kernel_src_sha, steps_per_launch=1):
+def _profile_name(steps_per_launch=1, edge=256):
+    """Committed ncu summary of the FP32 update kernel on an edge^3 lattice."""
+    kernel = "update2_slab" if steps_per_launch == 2 else "update_rows"
+    return "%s_d3q7_f32_%dcubed.md" % (kernel, edge)
+
+
+def _traffic(kernel_src_sha, steps_per_launch=1, edge=256):
     """Per-launch DRAM bytes of the update kernel from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
-    name = "update2_slab_d3q7_f32_256cubed.md" if steps_per_launch == 2 else "update_rows_d3q7_f32_256cubed.md"
-    path = os.path.join(ROOT, "profiles", name)
+    path = os.path.join(ROOT, "profiles", _profile_name(steps_per_launch, edge))
     try:
         text = open(path).read()
     except OSError:
@@ -198,37 +213,51 @@ def cpu_baseline_mlp(sur, q, n=65536):
                       % (len(x), dt)}
 
 
-def run_reference(args, prob):
+def step_problems(args):
+    """The problems of the timed workload, one per bench step in turn: the 16
+    positions of the 512^3 sweep, or the single 256^3 sphere."""
+    if args.workload == "sphere512":
+        return [workloads.sphere_3d_large(position=j, precision=args.precision) for j in range(16)]
+    return [workloads.sphere_3d(seed=args.seed, precision=args.precision)]
+
+
+def run_reference(args, probs):
     rank, world, _ = _dist()
     if rank != 0:
         return
     import oracle
     oracle.build.build()
+    prob = probs[0]
     cells = prob["n"][0] * prob["n"][1] * prob["n"][2]
-    per_step = 6  # LB steps per bench step: bounded so K + W steps take minutes
-    sample = dict(prob, n_steps=per_step, n_window=per_step // 3)
-    for _ in range(args.warmup):
+    # LB steps per bench step (a third sampled, setup included): bounded so
+    # that K + W steps take minutes
+    per_step = 3 if cells > 256 ** 3 else 6
+    t_all = 0.0
+    for i in range(args.warmup + args.steps):
+        p = probs[i % len(probs)]
+        sample = dict(p, n_steps=per_step, n_window=per_step // 3)
+        t0 = time.perf_counter()
         oracle.run(sample)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.run(sample)
-    dt = time.perf_counter() - t0
-    value = cells * per_step * args.steps / dt / 1e9
+        if i >= args.warmup:
+            t_all += time.perf_counter() - t0
+    value = cells * per_step * args.steps / t_all / 1e9
+    sample_txt = "%d LB steps (%d sampled) of the %dx%dx%d lattice per step, setup included" % (
+        per_step, per_step // 3, *prob["n"])
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " (oracle: %d LB steps per step)" % per_step,
+        "config": {"workload": WORKLOADS[args.workload] + " (oracle: %d LB steps per step)" % per_step,
                    "l2": "inputs larger than L2"},
         "cpu_baseline": {"kind": "oracle", "cores": oracle.threads(), "value": value, "unit": "GLUPS",
-                         "sample": "%d LB steps of the 256^3 lattice per step, setup included" % per_step},
+                         "sample": sample_txt},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, prob):
+def run_gpu(args, probs):
     import ctypes
 
     import torch
@@ -243,18 +272,35 @@ def run_gpu(args, prob):
         dist.init_process_group("nccl")
     B.build()
     stream = torch.cuda.Stream()
-    cells = prob["n"][0] * prob["n"][1] * prob["n"][2]
-    solver = wlb.Solver(prob, stream=stream)
-    if args.single_step:
-        solver.set_two_step(False)
-    elif args.slab_rows:
-        solver.set_two_step(True, args.slab_rows)
-    info = solver.info()
+    prob0 = probs[0]
+    cells = prob0["n"][0] * prob0["n"][1] * prob0["n"][2]
+    edge = prob0["n"][0]
+
+    def make(prob):
+        s = wlb.Solver(prob, stream=stream)
+        if args.single_step:
+            s.set_two_step(False)
+            return s
+        if args.tiles:
+            s.set_two_step_tiles(args.tiles)
+        if args.slab_rows:
+            s.set_two_step(True, args.slab_rows)
+        return s
+
+    # one handle for a fixed problem; a new one per position otherwise (the
+    # setup differs; creating it is part of the position's force evaluation)
+    fixed = make(prob0) if len(probs) == 1 else None
+    if fixed is not None:
+        info = fixed.info()
+    else:
+        with make(prob0) as s:
+            info = s.info()
     n_steps, n_window = info.n_steps, info.n_window
     n_free = n_steps - n_window
     n_avg = n_window // info.period
 
-    def one_step(ev=None):
+    def one_step(i, ev=None):
+        solver = fixed or make(probs[i % len(probs)])
         solver.init()
         if ev is not None:
             ev[0].record(stream)
@@ -262,10 +308,13 @@ def run_gpu(args, prob):
         if ev is not None:
             ev[1].record(stream)
         solver.step(n_window, sample=True)
-        return solver.force()
+        F = solver.force()
+        if fixed is None:
+            solver.close()
+        return F
 
-    for _ in range(args.warmup):
-        F = one_step()
+    for i in range(args.warmup):
+        one_step(i)
 
     def barrier():
         if world > 1:
@@ -279,9 +328,10 @@ def run_gpu(args, prob):
     end = torch.cuda.Event(enable_timing=True)
     k1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    forces = []
     start.record(stream)
     for i in range(args.steps):
-        F = one_step(k1[i])
+        forces.append(one_step(i, k1[i]))
     end.record(stream)
     barrier()
     clk = clocks.stop()
@@ -293,13 +343,15 @@ def run_gpu(args, prob):
     ms, lu = job_totals(ms, cells * n_steps * args.steps, world, device="cuda")
     glups = lu / (ms * 1e-3) / 1e9
     forces_per_s = lu / (cells * n_steps) / (ms * 1e-3)
+    if fixed is not None:
+        fixed.close()
 
     # end to end through the public API: host parameters in, host force out
     e2e_steps = max(1, min(args.steps, 2))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        Fe = wlb.compute_force(prob)
+    for i in range(e2e_steps):
+        Fe = wlb.compute_force(probs[i % len(probs)])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": cells * n_steps * e2e_steps * world / e2e_s / 1e9, "unit": "GLUPS",
@@ -317,38 +369,52 @@ def run_gpu(args, prob):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    traffic = _traffic(_kernel_sha(spl), spl) if args.precision == "f32" else None
-    # per force: 3 setup kernels, one update launch per step (sampling fused into
-    # it on the row-vectorised path), per averaged period a fold and the two
-    # launches that record its force in the history, the force
-    per_step = 3 + n_window + n_free // spl + (0 if info.vector_path else n_window) + 3 * n_avg + 1
+    traffic = _traffic(_kernel_sha(spl), spl, edge) if args.precision == "f32" else None
+    # lattice updates per second if every launch moved exactly its algorithmic
+    # bytes at the measured copy bandwidth (one pass over the state per launch)
+    glups_bound = peak / (bpu / spl)
+    # per force: 3 setup kernels, one update launch per step pair (sampled
+    # launches add their sampling kernel; one per step on the row-vectorised
+    # one-step path is fused), per averaged period a fold and the two launches
+    # that record its force in the history, the force
+    if spl == 2:
+        per_step = 3 + n_free // 2 + 2 * (n_window // 2) + 3 * n_avg + 1
+    else:
+        per_step = 3 + n_window + n_free + (0 if info.vector_path else n_window) + 3 * n_avg + 1
     launches = args.steps * per_step
     if rank == 0:
+        positions = sorted({i % len(probs) for i in range(args.steps)})
         line = {
             "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"f32": "f32", "f64": "f64", "f16": "f16 storage, f32 arithmetic"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": cells, "lb_steps_per_force": n_steps,
-                       "window_steps": n_window, "kappa_ratio": prob.get("kappa"),
+            "config": {"workload": WORKLOADS[args.workload], "cells": cells, "lb_steps_per_force": n_steps,
+                       "window_steps": n_window, "kappa_ratio": prob0.get("kappa"),
+                       "positions_timed": len(positions) if len(probs) > 1 else 1,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs (2 x 470 MB populations) larger than L2; no flush"},
+                       "l2": "inputs (2 x %.2f GB populations) larger than L2; no flush"
+                             % (7 * cells * {"f32": 4, "f16": 2, "f64": 8}[args.precision] / 1e9)},
             "forces_per_s": forces_per_s,
-            "force": [float(v) for v in F],
+            "force": [float(v) for v in forces[0]],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
-                         "kernel": ("update2_slab, 2 steps/launch, %d-row slabs" % info.two_step_rows
+                         "kernel": ("update2_slab, 2 steps/launch, %d-row slabs, %d x-tile%s per row"
+                                    % (info.two_step_rows, info.two_step_tiles, "" if info.two_step_tiles == 1 else "s")
                                     if spl == 2 else "update_rows")
                                    + " (%s storage)" % args.precision, "bytes_per_cell_per_launch": bpu,
-                         "avg_launch_us": k1_ms * 1e3, "peak_source": peak_src + " hbm_gbs"},
+                         "steps_per_launch": spl, "avg_launch_us": k1_ms * 1e3,
+                         "glups_bound": glups_bound, "glups_frac_of_bound": glups / (world * glups_bound),
+                         "peak_source": peak_src + " hbm_gbs"},
             "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
+        if len(probs) > 1:
+            line["forces_by_position"] = {str(i % len(probs)): float(F[2]) for i, F in enumerate(forces)}
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(prob)
+            line["cpu_baseline"] = cpu_baseline(prob0, steps=12 if cells > 256 ** 3 else None)
         print(json.dumps(line), flush=True)
-    solver.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -653,25 +719,38 @@ def run_sweep(args):
 
 def run_profile(args, prob):
     """A short pass over the benchmark lattice for ncu: setup, 64 unsampled and
-    64 sampled steps (graph-replayed where whole periods allow), the force."""
+    64 sampled steps (graph-replayed where whole periods allow), the force.
+    --profile-nz cuts the lattice along z (same rows, planes and slab plan per
+    plane; fewer planes) for captures that must stay within a few GB."""
     import torch
 
     import paper_2404_02346_gb300 as wlb
     from paper_2404_02346_gb300 import build as B
 
     B.build()
+    if args.profile_nz:
+        nx, ny, _ = prob["n"]
+        lam = float(args.profile_nz)  # one wavelength along the cut axis
+        prob = workloads.problem(3, (nx, ny, args.profile_nz), 2, lam, prob["radius"],
+                                 (nx / 2, ny / 2, lam / 8), cp=prob["cp"], n_surface=prob["n_surface"],
+                                 n_periods=1, n_avg_periods=1, precision=prob["precision"])
     stream = torch.cuda.Stream()
     with wlb.Solver(prob, stream=stream) as s:
         if args.single_step:
             s.set_two_step(False)
-        elif args.slab_rows:
-            s.set_two_step(True, args.slab_rows)
+        else:
+            if args.tiles:
+                s.set_two_step_tiles(args.tiles)
+            if args.slab_rows:
+                s.set_two_step(True, args.slab_rows)
+        info = s.info()
         s.init()
         s.step(args.profile_steps, sample=False)
         s.step(args.profile_steps, sample=True)
         F = s.force()
-    print(json.dumps({"profile_run": True, "force": [float(v) for v in F],
-                      "launches": 2 + 3 * args.profile_steps + 2}))
+    print(json.dumps({"profile_run": True, "shape": list(prob["n"]), "force": [float(v) for v in F],
+                      "steps_per_launch": info.steps_per_launch, "slab_rows": info.two_step_rows,
+                      "segments": info.two_step_segments, "tiles": info.two_step_tiles}))
 
 
 def main():
@@ -685,33 +764,37 @@ def main():
     ap.add_argument("--single-step", action="store_true",
                     help="one step per update launch (default: unsampled steps two per launch)")
     ap.add_argument("--slab-rows", type=int, default=0, help="slab height of the two-step kernel (0: automatic)")
+    ap.add_argument("--tiles", type=int, default=0,
+                    help="x-tiles per row of the two-step kernel (0: automatic, 1: whole rows)")
     ap.add_argument("--profile", action="store_true", help="short pass for ncu captures")
     ap.add_argument("--profile-steps", type=int, default=64)
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"],
                     help="population storage (the benchmark workload is FP32)")
-    ap.add_argument("--workload", default="sphere256",
-                    choices=["sphere256", "ensemble3d", "ensemble2d", "surrogate", "surrogate_infer", "sweep512"],
-                    help="sphere256: the benchmark line; ensembles: batched forces/s; surrogate: learned model "
-                         "(surrogate_infer: its inference alone)")
+    ap.add_argument("--workload", default="sphere512",
+                    choices=["sphere512", "sphere256", "ensemble3d", "ensemble2d", "surrogate", "surrogate_infer",
+                             "sweep512"],
+                    help="sphere512: the benchmark line (512^3, one sweep position per step); sphere256: the "
+                         "256^3 sphere; ensembles: batched forces/s; surrogate: learned model (surrogate_infer: "
+                         "its inference alone); sweep512: all 16 positions per storage precision in one line")
     ap.add_argument("--epochs", type=int, default=1500, help="surrogate training epochs")
     ap.add_argument("--queries", type=int, default=1 << 20, help="surrogate inference queries")
     ap.add_argument("--positions", type=int, default=16, help="sweep512: the first N of the 16 positions")
+    ap.add_argument("--profile-nz", type=int, default=0, help="--profile: planes of a z-cut lattice (0: full)")
     args = ap.parse_args()
-    prob = workloads.sphere_3d(seed=args.seed, precision=args.precision)
-    if args.profile:
-        run_profile(args, prob)
-    elif args.workload == "surrogate":
+    if args.workload == "surrogate":
         run_surrogate(args)
     elif args.workload == "surrogate_infer":
         run_surrogate_infer(args)
     elif args.workload == "sweep512":
         run_sweep(args)
-    elif args.workload != "sphere256":
+    elif args.workload in ("ensemble3d", "ensemble2d"):
         run_ensemble(args)
+    elif args.profile:
+        run_profile(args, step_problems(args)[0])
     elif args.impl == "reference":
-        run_reference(args, prob)
+        run_reference(args, step_problems(args))
     else:
-        run_gpu(args, prob)
+        run_gpu(args, step_problems(args))
 
 
 if __name__ == "__main__":

@@ -139,7 +139,8 @@ typedef struct {
                                    wlb_set_two_step (the default for 3D
                                    lattices where it applies)                   */
     int two_step_rows;          /* slab height of the two-step kernel, 0 off    */
-    int two_step_segments;      /* warps per lattice row in it, 0 off           */
+    int two_step_segments;      /* warps per lattice row (per x-tile) in it, 0 off */
+    int two_step_tiles;         /* x-tiles per row in it (1: whole rows), 0 off */
 } wlb_info;
 
 /* Check a parameter set.  WLB_ERR_ARG for: unknown lattice or precision,
@@ -263,15 +264,18 @@ wlb_status wlb_force_history(wlb_handle *h, double *out, long long *samples_out,
  * Allocation-free averaging (the paper has no counterpart of this call).
  *
  * For callers that cannot allocate device memory when they need a force:
- * code running while a CUDA graph is captured in global mode (an allocation
- * would invalidate the capture), processes whose device memory belongs to a
- * fixed pool under a hard budget, and latency-bound loops that must not wait
- * on an allocator.  Starting from the handle's current state, advances
- * n_steps >= 0 sampled steps exactly as wlb_step(h, n_steps, 1) does
- * (interpolation, running sums folded to FP64 once per period, fused
- * stream+collide) and then returns the time-averaged force over those
+ * processes whose device memory is a fixed pool owned by someone else (a
+ * framework's caching allocator that has reserved the whole budget, or an
+ * arena handed to a plugin that is given no allocator of its own), and loops
+ * that cannot afford cudaMalloc / cudaFree, which may synchronise the whole
+ * device.  Starting from the handle's current state, advances n_steps >= 0
+ * sampled steps exactly as wlb_step(h, n_steps, 1) does (interpolation,
+ * running sums folded to FP64 once per period, fused stream+collide, one
+ * step per launch) and then returns the time-averaged force over those
  * n_steps, as wlb_force would for them, in force_out (3 host doubles; zeros
- * when n_steps == 0 or n_surface == 0).  Synchronises the handle's stream.
+ * when n_steps == 0 or n_surface == 0).  The result equals wlb_step +
+ * wlb_force over the same steps bit for bit.  Synchronises the handle's
+ * stream.
  *
  * It calls no cudaMalloc, cudaFree or allocating library routine and
  * instantiates no graph: kernels are launched directly, and the running
@@ -280,9 +284,10 @@ wlb_status wlb_force_history(wlb_handle *h, double *out, long long *samples_out,
  * loading the library holds until the process exits.  The handle's own
  * accumulators and sample counters are left untouched.
  *
- *   - The first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress, with that device current); make this first call
- *     before any stream capture.
+ *   - The first call on a device (and the first after the device's context
+ *     was reset) looks up that array's device address (cudaGetSymbolAddress,
+ *     with that device current); make this first call before any stream
+ *     capture.
  *   - All calls share the array, which keeps the last call's contents; each
  *     call clears what it accumulates before use.  Calls whose work overlaps
  *     on the GPU (other streams, other threads, other handles) race on it:
@@ -432,8 +437,8 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
  * up by wlb_create with an automatic slab height) wherever it is supported:
  * 3D, periodic boundaries, FP32 or FP16 storage, nx a multiple of 16 cells
  * (each row split into warp-wide segments, the last one possibly shorter),
- * and at least one slab row fitting the shared memory (nx up to about 1500
- * FP32 cells).
+ * and rows that fit the shared memory whole (nx up to about 1500 FP32
+ * cells) or split into x-tiles (wlb_set_two_step_tiles).
  * 2D lattices (periodic, any storage, rows of at most two 16-byte chunks
  * per lane and 8 values per lane) take it on request (off by default: a
  * single lattice of such short rows has too few row chunks to fill the SMs
@@ -450,6 +455,27 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out);
  * wait) makes wlb_force return WLB_ERR_TIMEOUT.  The paper has no counterpart:
  * it is a memory-traffic optimisation of the same update. */
 wlb_status wlb_set_two_step(wlb_handle *h, int enable, int slab_rows);
+
+/* x-tiles of the two-step kernel (3D).  A slab's rows are staged in shared
+ * memory, so long rows leave room only for short slabs, and every slab
+ * recomputes two halo rows: 512-cell FP32 rows allow 3-row slabs.  Splitting
+ * each row into tiles of tx cells (a multiple of 16; the last tile may be
+ * narrower) lets a CTA hold a taller slab of one tile; it stages 16 bytes of
+ * every array on either side of its tile and also computes the first step on
+ * the two cells just outside it, so no CTA waits for another.  Bit-identical
+ * to whole rows.  The tiles' rows are staged by per-thread copies, which
+ * cost instructions that whole rows do not: measured slower wherever a
+ * whole-row slab fits (512^3 FP32: 1410 us per launch with 4 tiles of 14-row
+ * slabs against 1254 us with 3-row whole-row slabs).  tiles: 0 lets the
+ * library choose (whole rows where a whole-row slab fits the shared memory,
+ * else the cheapest estimate of 2 .. 16 tiles: rows of more than about 1500
+ * FP32 cells), 1 whole rows, n >= 2 n tiles of ceil(nx / n) cells rounded up
+ * to 16, each at most one warp of 16-byte vectors (two per lane for FP32).  Applies to the current and
+ * later wlb_set_two_step settings.  WLB_ERR_STATE while two steps per launch
+ * is off; WLB_ERR_ARG if the tiling does not fit (setting unchanged) or on a
+ * 2D lattice (tiles > 1).  The paper has no counterpart: it changes how the
+ * same update is scheduled, not what it computes. */
+wlb_status wlb_set_two_step_tiles(wlb_handle *h, int tiles);
 
 /* Release the handle, its graphs, streams and any memory it allocated. */
 wlb_status wlb_destroy(wlb_handle *h);

@@ -50,3 +50,21 @@ def lattice_omega(k, c2):
     For k -> 0 this gives w = c |k| (Eq. 68 with the local sound speed)."""
     s = c2 * sum(math.sin(0.5 * ka) ** 2 for ka in k)
     return 2.0 * math.asin(math.sqrt(s))
+
+
+def volume_ratio(dim, R, c0, cp, d=4.0):
+    """Compressibility volume of the smooth object of Eq. (79) over that of the
+    sharp one: int (1 - kappa(r)/kappa0) dV / ((1 - kappa~) V_R), with
+    kappa = 1/c^2 (density matched).  The monopole strength of Eq. (24)
+    integrated over a graded object is proportional to the numerator, so the
+    closed forms of Eqs. (83a, b) for the smooth object carry this factor."""
+    from scipy.integrate import quad
+
+    def g(r):
+        c = cp + 0.5 * (c0 - cp) * (1 + math.tanh((r * r - R * R) / d))
+        return 1 - c0 * c0 / (c * c)
+
+    kap = c0 * c0 / (cp * cp)
+    if dim == 2:
+        return quad(lambda r: g(r) * 2 * math.pi * r, 0, R + 30, limit=400)[0] / ((1 - kap) * math.pi * R * R)
+    return quad(lambda r: g(r) * 4 * math.pi * r * r, 0, R + 30, limit=400)[0] / ((1 - kap) * 4 / 3 * math.pi * R ** 3)

@@ -57,6 +57,7 @@ class Info(ctypes.Structure):
         ("steps_per_launch", ctypes.c_int),
         ("two_step_rows", ctypes.c_int),
         ("two_step_segments", ctypes.c_int),
+        ("two_step_tiles", ctypes.c_int),
     ]
 
 
@@ -99,6 +100,7 @@ _SIGNATURES = {
     "wlb_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "wlb_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(Info)]),
     "wlb_set_two_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "wlb_set_two_step_tiles": (ctypes.c_int, [_VP, ctypes.c_int]),
     "wlb_destroy": (ctypes.c_int, [_VP]),
     "wlb_average_noalloc": (ctypes.c_int, [_VP, ctypes.c_longlong, _DP]),
     "wlb_batch_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int,
@@ -247,6 +249,11 @@ class Solver:
         library choose, 1 or 2 asks for that lane layout."""
         mode = (1 + int(chunks_per_lane)) if enable else 0
         _check(lib().wlb_set_two_step(self._h, mode, int(slab_rows)), self._h, "wlb_set_two_step")
+
+    def set_two_step_tiles(self, tiles=0):
+        """x-tiles per row of the two-step kernel (wlb_set_two_step_tiles): 0
+        lets the library choose, 1 keeps whole rows, n splits rows in n."""
+        _check(lib().wlb_set_two_step_tiles(self._h, int(tiles)), self._h, "wlb_set_two_step_tiles")
 
     def step(self, n, sample=False):
         _check(lib().wlb_step(self._h, int(n), 1 if sample else 0), self._h, "wlb_step")

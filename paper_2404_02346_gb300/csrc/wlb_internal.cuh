@@ -84,17 +84,20 @@ bool update_is_vectorised(const Geometry &g, Prec p);
 // Two steps per launch (wlb_two_step.cu): 3D, periodic, FP32 or FP16 rows
 // that are whole numbers of warp-wide 16-byte vectors, split into nseg
 // segments of one warp each.  Slab height H, slabs and z-chunks of the grid,
-// segments per row, chunks per lane, block size and dynamic shared memory.
+// segments per row (per x-tile when rows are split into ntile tiles of tx
+// cells), chunks per lane, block size and dynamic shared memory.
 struct TwoStepPlan {
     int H = 0, nslab = 0, chunks = 0, zc = 0, nseg = 0, chunks_per_lane = 0, threads = 0;
-    bool full = false;  // every segment a full warp (no idle lanes)
+    int ntile = 1, tx = 0;  // x-tiles per row and their width (1: whole rows)
+    bool full = false;      // every segment a full warp (no idle lanes)
     size_t smem = 0;
 };
 bool two_step_supported(const Geometry &g, Prec p);
 // slab_rows: 0 picks H; otherwise that H.  mode: 1 automatic, 2 one 16-byte
-// chunk per lane, 3 two.  Also opts the kernel into the shared memory it needs
-// on the current device.
-cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, TwoStepPlan *out);
+// chunk per lane, 3 two.  tiles: 0 automatic, 1 whole rows, n >= 2 n x-tiles
+// per row.  Also opts the kernel into the shared memory it needs on the
+// current device.
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, TwoStepPlan *out);
 // Side stream and events that let the sampling kernel of a sampled two-step
 // launch run beside the update (fork before, join after).
 struct SideStream {

@@ -1,15 +1,17 @@
 // wlb_average_noalloc: time averaging and force without any allocation.
 //
 // The paper has no counterpart of this entry point.  It exists for callers that
-// cannot allocate device memory at the point where they need a force: code that
-// runs while a CUDA graph is being captured in global mode (an allocation there
-// invalidates the capture), processes whose device memory is owned by a fixed
-// pool under a hard budget, and latency-bound loops that must not block on the
-// allocator.  It runs the same sampling, fold and force kernels as
-// wlb_step(sample = 1) + wlb_force, with direct launches (no graph is
-// instantiated, which would allocate) and with the running sums, their FP64
-// totals, the force and the error flag in one file-scope device array instead
-// of the handle's workspace.
+// cannot allocate device memory at the point where they need a force: processes
+// whose device memory is a fixed pool owned by someone else (a framework's
+// caching allocator that has reserved the whole budget, an arena handed to a
+// plugin that is given no allocator of its own), and loops that cannot afford
+// cudaMalloc / cudaFree, which may synchronise the whole device.  It runs the
+// same sampling, fold and force kernels as wlb_step(sample = 1) + wlb_force,
+// launched directly (instantiating a graph would allocate), with the running
+// sums, their FP64 totals, the force and the error flag in one file-scope
+// device array instead of the handle's workspace.
+#include <cuda.h>
+
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -28,20 +30,59 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchAddress {
+    unsigned long long context = 0;  // id of the context the address belongs to (0: none yet)
+    void *addr = nullptr;
+};
+ScratchAddress g_scratch_addr[kMaxDevices];
 
-// Device address of g_scratch on `device` (which must be current), looked up
-// once per device.  The host-side symbol is not a device address.
+// Driver calls that identify the current context, resolved through the
+// runtime (no link against the driver library).
+using CtxGetCurrent = CUresult(CUDAAPI *)(CUcontext *);
+using CtxGetId = CUresult(CUDAAPI *)(CUcontext, unsigned long long *);
+CtxGetCurrent g_ctx_get_current = nullptr;
+CtxGetId g_ctx_get_id = nullptr;
+
+cudaError_t resolve_driver_calls() {
+    if (g_ctx_get_current && g_ctx_get_id) return cudaSuccess;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+        return cudaErrorSymbolNotFound;
+    g_ctx_get_current = (CtxGetCurrent)f1;
+    g_ctx_get_id = (CtxGetId)f2;
+    return cudaSuccess;
+}
+
+// Device address of g_scratch on `device` (which must be current).  The
+// host-side symbol is not a device address.  The address is looked up once
+// per device and context: the module holding the array is loaded per
+// context, so after a cudaDeviceReset (a new primary context) it is looked up
+// again rather than reused.
 cudaError_t scratch_address(int device, void **out) {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[device] = p;
+    cudaError_t e = resolve_driver_calls();
+    if (e != cudaSuccess) return e;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+    if (!ctx) {  // no context current on this thread yet: make the primary one current
+        if ((e = cudaSetDevice(device)) != cudaSuccess) return e;
+        if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorContextIsDestroyed;
     }
-    *out = g_scratch_addr[device];
+    unsigned long long id = 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+    ScratchAddress &slot = g_scratch_addr[device];
+    if (slot.context != id || !slot.addr) {
+        void *p = nullptr;
+        if ((e = cudaGetSymbolAddress(&p, g_scratch)) != cudaSuccess) return e;
+        slot.addr = p;
+        slot.context = id;
+    }
+    *out = slot.addr;
     return cudaSuccess;
 }
 

@@ -26,6 +26,19 @@
 // slabs read at the same time (L2 hits).  Results are bit-identical to two single steps: the same
 // per-cell arithmetic, and the t+1 values are rounded to the storage type as
 // a single step would store them.
+//
+// Wide rows (x-tiles).  Shared memory bounds the slab height by the row
+// length (512-cell FP32 rows leave room for 3-row slabs, so 5 S1 rows are
+// computed per 3 output rows).  A plan may instead split each row into
+// ntile tiles of tx cells, one warp per tile row (slab_body_tiled): a CTA
+// owns one tile of its slab and stages the tile plus one 16-byte vector of
+// every array on either side (wrapped around x at the row's ends), and
+// computes S1 also on the two halo cells x = xa - 1 and x = xb, whose +x and
+// -x values are the ones S2 pulls across the tile's ends.  The tile's rows
+// are not contiguous in memory, so instead of bulk copies every warp stages
+// its own row with per-thread 16-byte cp.async copies.  That staging costs
+// the compute warps instructions that the bulk copies do not, so the
+// automatic plan splits only rows too long for any whole-row slab.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -54,6 +67,22 @@ constexpr int two_step_threads() {
 // populations (storage type).
 constexpr size_t smem_per_row(size_t row_bytes, size_t c2_row_bytes, size_t cls_row_bytes) {
     return (size_t)kStages * (7 * row_bytes + c2_row_bytes + cls_row_bytes) + (size_t)kRingPlanes * 2 * row_bytes;
+}
+
+// Halo cells staged on either side of an x-tile: 16 bytes of each array.
+template <typename S> constexpr int halo_pop() { return 16 / (int)sizeof(S); }
+template <typename S> constexpr int halo_c2() { return 16 / (int)sizeof(typename Store<S>::R); }
+constexpr int kHaloCls = 16;
+
+// Shared memory per S1 row of a tiled plan (tiles of tx cells, one warp
+// per tile row): two staged planes of tx + 2 halo cells of every array and
+// the three-plane exchange ring of tx cells.
+template <typename S>
+constexpr size_t smem_per_tile_row(int tx) {
+    using R = typename Store<S>::R;
+    return (size_t)kStages * (7 * (size_t)(tx + 2 * halo_pop<S>()) * sizeof(S) +
+                              (size_t)(tx + 2 * halo_c2<S>()) * sizeof(R) + (size_t)(tx + 2 * kHaloCls)) +
+           (size_t)kRingPlanes * 2 * (size_t)tx * sizeof(S);
 }
 
 template <typename S> struct Vec;  // plain 16-byte shared-memory accesses
@@ -252,6 +281,7 @@ struct SlabParams {
     long long ncell;
     typename Store<S>::R c0sq, cpsq;
     int H, nslab, zc, nseg;  // plan
+    int ntile, tx;           // x-tiles per row and their width in cells (ntile = 1: whole rows)
     int *err;
 };
 
@@ -509,10 +539,281 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
     }
 }
 
+// 16-byte asynchronous copy global -> shared by one thread (both 16-byte
+// aligned), its commit and the wait for all but the newest N groups.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The x-tiled sweep of CTA `cta`: x-tile cta % ntile (cells xa .. xa+tw-1 of
+// every row), slab c % nslab and z-chunk c / nslab of c = cta / ntile.  One
+// warp per S1 row (a tile row is at most 32 * CH vectors), so a warp reads
+// only the staged row it stages itself: each lane copies its 16-byte vectors
+// of the row, the tile plus one vector of populations (and of c^2, and 16
+// class bytes) on either side, wrapped around x at the row's ends, with
+// cp.async two planes ahead (one commit group per plane), and waits for its
+// own groups.  The block barrier per plane is the +-y exchange's.  S1 also
+// runs on the halo cells x = xa - 1 (lane 0; its +x value is S2's pull into
+// xa) and x = xb (the lane holding the row's last vector; its -x value is
+// S2's pull into xb - 1), kept in those lanes' registers until S2 of the
+// plane.  Arithmetic as in slab_body, so results are bit-identical.
 template <typename S, int CH, bool FULL>
+__device__ __forceinline__ void slab_body_tiled(const SlabParams<S> &P, int cta, unsigned char *smem) {
+    using R = typename Store<S>::R;
+    constexpr int W = Store<S>::W;
+    constexpr int HP = halo_pop<S>();  // halo cells per side: populations (one vector),
+    constexpr int HQ = halo_c2<S>();   // c^2 (one vector),
+    constexpr int HC = kHaloCls;       // class bytes (one vector)
+    static_assert(HP == W && HQ == 16 / (int)sizeof(R), "one 16-byte vector on either side");
+    constexpr int QW = 16 / (int)sizeof(R);                // c^2 values per 16-byte vector
+    constexpr int NJ = (32 * CH + 2 + 31) / 32;            // population vectors per lane and row, at most
+    constexpr int NQ = (32 * CH * W / QW + 2 + 31) / 32;   // c^2 vectors per lane and row, at most
+    const S *__restrict__ A = P.A;
+    S *__restrict__ B = P.B;
+    const uint8_t *__restrict__ cls = P.cls;
+    const uint8_t *__restrict__ band_rows = P.band_rows;
+    const R *__restrict__ c2f = P.c2f;
+    const int nx = P.nx, ny = P.ny, nz = P.nz, H = P.H, nslab = P.nslab, zc = P.zc, ntile = P.ntile, tx = P.tx;
+    const long long ncell = P.ncell;
+    const R c0sq = P.c0sq, cpsq = P.cpsq;
+    const int rmax = H + 2;
+    const int tile = cta % ntile, ct = cta / ntile;
+    const int slab = ct % nslab, chunk = ct / nslab;
+    const int xa = tile * tx, tw = min(tx, nx - xa);
+    const size_t pit_s = (size_t)tx + 2 * HP, pit_q = (size_t)tx + 2 * HQ, pit_c = (size_t)tx + 2 * HC;
+    S *stage = reinterpret_cast<S *>(smem);                                          // [kStages][7][rmax][pit_s]
+    R *c2s = reinterpret_cast<R *>(stage + (size_t)kStages * 7 * rmax * pit_s);      // [kStages][rmax][pit_q]
+    uint8_t *clss = reinterpret_cast<uint8_t *>(c2s + (size_t)kStages * rmax * pit_q);  // [kStages][rmax][pit_c]
+    S *ring = reinterpret_cast<S *>(clss + (size_t)kStages * rmax * pit_c);         // [kRingPlanes][2][rmax][tx]
+
+    const int y0 = slab * H;
+    const int hs = min(H, ny - y0);  // rows of this slab
+    const int rs = hs + 2;           // S1 rows
+    const int za = chunk * zc, zb = min(nz, za + zc);
+    if (za >= zb) return;            // whole block: empty chunk
+    const int L = zb - za + 2;       // S1 planes za-1 .. zb
+    const int row = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp = S1 row y0-1+row
+    const bool s1_row = row < rs;
+    const bool s2_row = row >= 1 && row <= hs;
+    const int y = (y0 - 1 + row + ny) % ny;
+    const int vg = FULL ? 32 * CH : min(32 * CH, tw / W);  // vectors of the tile row
+    const int rl = (vg - 1) & 31;                          // lane holding its last vector
+    bool act[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) act[c] = FULL || c * 32 + lane < vg;
+
+    // this lane's staging vectors: v = lane + 32 j of the row (v = 0 and the
+    // last one are the halo vectors), as wrapped global x of their first cell
+    auto wrapx = [&](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
+    const int nv_s = tw / W + 2, nv_q = tw / QW + 2, nv_c = tw / 16 + 2;
+    int gs[NJ], gq[NQ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int v = lane + 32 * j;
+        gs[j] = v < nv_s ? wrapx(xa - HP + v * W) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        const int v = lane + 32 * j;
+        gq[j] = v < nv_q ? wrapx(xa - HQ + v * QW) : -1;
+    }
+    const int gc = lane < nv_c ? wrapx(xa - HC + lane * 16) : -1;
+    auto band_flag = [&](int k) -> int {
+        if (k >= L) return 0;
+        return band_rows[(long long)((za - 1 + k + nz) % nz) * ny + y];
+    };
+    // stage this warp's S1 row of plane index k (plane za-1+k) into stage k % 2
+    auto stage_row = [&](int k, int flag) {
+        const int p = (za - 1 + k + nz) % nz;
+        const int buf = k % kStages;
+        S *dst0 = stage + ((size_t)buf * 7 * rmax + row) * pit_s;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            const int dy = i == 3 ? -1 : (i == 4 ? 1 : 0);  // +y pulls from y-1, -y from y+1
+            const int pp = i == 5 ? (p + nz - 1) % nz : (i == 6 ? (p + 1) % nz : p);
+            const S *src = A + (long long)i * ncell + ((long long)pp * ny + (y + dy + ny) % ny) * nx;
+            S *dst = dst0 + (size_t)i * rmax * pit_s;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j)
+                if (gs[j] >= 0) cp_async16(dst + (size_t)(lane + 32 * j) * W, src + gs[j]);
+        }
+        const long long rowp = ((long long)p * ny + y) * nx;
+        if (gc >= 0) cp_async16(clss + ((size_t)buf * rmax + row) * pit_c + (size_t)lane * 16, cls + rowp + gc);
+        if (flag) {
+            R *dq = c2s + ((size_t)buf * rmax + row) * pit_q;
+#pragma unroll
+            for (int j = 0; j < NQ; ++j)
+                if (gq[j] >= 0) cp_async16(dq + (size_t)(lane + 32 * j) * QW, c2f + rowp + gq[j]);
+        }
+        cp_async_commit();
+    };
+
+    // band flags of the staged planes k, k + 1 and of plane k + 2 (next issue)
+    int f0 = 0, f1 = 0, fn = 0;
+    if (s1_row) {
+        f0 = band_flag(0);
+        f1 = band_flag(1);
+        stage_row(0, f0);
+        stage_row(1, f1);  // L >= 3
+        fn = band_flag(2);
+    }
+    // registers carried between planes (S1 results in storage precision)
+    R n0[CH][W], n1[CH][W], n2[CH][W];  // rest, +x, -x of plane p-1
+    R pz0[CH][W], pz1[CH][W];           // +z of planes p-2, p-1
+    R cq[CH][W];                        // c^2 of plane p-1
+    R hl = R(0), hr = R(0);             // +x at xa - 1 (lane 0), -x at xb (lane rl) of plane p-1
+    for (int k = 0; k < L; ++k) {
+        const int p = (za - 1 + k + nz) % nz;
+        const int buf = k % kStages;
+        R c0v[CH][W], c1v[CH][W], c2v[CH][W], c5v[CH][W], c6v[CH][W];
+        R cs[CH][W];
+        R hl_new = R(0), hr_new = R(0);
+        if (s1_row) {
+            cp_async_wait<1>();  // this lane's copies of stage k (the newest group is stage k + 1)
+            __syncwarp();        // and the other lanes'
+            // staged row of population 0 (population i at + i * pst), indexed
+            // by tile cell (halo cells at -HP .. -1 and tw .. tw+HP-1)
+            const S *st = stage + ((size_t)buf * 7 * rmax + row) * pit_s + HP;
+            const R *cst = c2s + ((size_t)buf * rmax + row) * pit_q + HQ;
+            const uint8_t *clt = clss + ((size_t)buf * rmax + row) * pit_c + HC;
+            const size_t pst = (size_t)rmax * pit_s;
+            const bool band_row = f0 != 0;  // warp-uniform
+            R f[7][CH][W];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int x0 = (c * 32 + lane) * W;
+                if (act[c]) {
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) Vec<S>::ld(st + (size_t)i * pst + x0, f[i][c]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 7; ++i)
+#pragma unroll
+                        for (int e = 0; e < W; ++e) f[i][c][e] = R(0);
+                }
+                const unsigned long long cl = act[c] ? load_classes<W>(clt + x0) : 0ull;
+                if (band_row) {
+#pragma unroll
+                    for (int e = 0; e < W; ++e) {
+                        const unsigned kc = (unsigned)(cl >> (8 * e)) & 0xffu;
+                        cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : (act[c] ? cst[x0 + e] : c0sq));
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < W; ++e)
+                        cs[c][e] = ((unsigned)(cl >> (8 * e)) & 0xffu) == CELL_FLUID ? c0sq : cpsq;
+                }
+            }
+            // the tile's ends pull from the staged halo cells
+            const R left = Vec<S>::get(st + pst - 1);        // +x at xa - 1
+            const R right = Vec<S>::get(st + 2 * pst + tw);  // -x at xb
+            R fpx[CH][W], fmx[CH][W];
+            shift_x<R, CH, W>(f[1], f[2], lane, vg, false, left, right, fpx, fmx);
+            S *ry = ring + ((size_t)(k % kRingPlanes) * 2 * rmax + row) * tx;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int x0 = (c * 32 + lane) * W;
+                R o[7][W];
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    R t[7];
+                    collide7(cs[c][e], f[0][c][e], fpx[c][e], fmx[c][e], f[3][c][e], f[4][c][e], f[5][c][e],
+                             f[6][c][e], t);
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) o[i][e] = t[i];
+                }
+                Vec<S>::rounded(o[0], c0v[c]);
+                Vec<S>::rounded(o[1], c1v[c]);
+                Vec<S>::rounded(o[2], c2v[c]);
+                Vec<S>::rounded(o[5], c5v[c]);
+                Vec<S>::rounded(o[6], c6v[c]);
+                const R (&oy)[W] = o[3];
+                const R (&omy)[W] = o[4];
+                if (act[c]) {
+                    Vec<S>::st(ry + x0, oy);                          // +y of row w
+                    Vec<S>::st(ry + (size_t)rmax * tx + x0, omy);     // -y of row w
+                }
+            }
+            // S1 on the halo cells x = -1 and x = tw
+            auto halo = [&](int x, int out) -> R {
+                const unsigned kc = clt[x];
+                const R c2h = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : cst[x]);
+                R t[7];
+                collide7(c2h, Vec<S>::get(st + x), Vec<S>::get(st + pst + x - 1), Vec<S>::get(st + 2 * pst + x + 1),
+                         Vec<S>::get(st + 3 * pst + x), Vec<S>::get(st + 4 * pst + x), Vec<S>::get(st + 5 * pst + x),
+                         Vec<S>::get(st + 6 * pst + x), t);
+                return Vec<S>::rounded(t[out]);
+            };
+            if (lane == 0) hl_new = halo(-1, 1);
+            if (lane == rl) hr_new = halo(tw, 2);
+            __syncwarp();  // every lane is done with stage k before it is refilled
+            if (k + 2 < L)
+                stage_row(k + 2, fn);
+            else
+                cp_async_commit();  // an empty group keeps one group per plane
+            f0 = f1;
+            f1 = fn;
+            fn = band_flag(k + 3);
+        }
+        __syncthreads();  // ring plane k written
+        if (k >= 2 && s2_row) {
+            const int q = (p + nz - 1) % nz;
+            const long long r0 = ((long long)q * ny + y) * nx + xa;
+            const S *ry = ring + (size_t)((k - 1) % kRingPlanes) * 2 * rmax * tx;
+            R fpx[CH][W], fmx[CH][W];
+            shift_x<R, CH, W>(n1, n2, lane, vg, false, hl, hr, fpx, fmx);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                if (!act[c]) continue;
+                const int x0 = (c * 32 + lane) * W;
+                R fpy[W], fmy[W];
+                Vec<S>::ld(ry + (size_t)(row - 1) * tx + x0, fpy);             // +y of row w-1
+                Vec<S>::ld(ry + (size_t)(rmax + row + 1) * tx + x0, fmy);      // -y of row w+1
+                R o[7][W];
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    R t[7];
+                    collide7(cq[c][e], n0[c][e], fpx[c][e], fmx[c][e], fpy[e], fmy[e], pz0[c][e], c6v[c][e], t);
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) o[i][e] = t[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 7; ++i) Store<S>::store(B + i * ncell + r0 + x0, o[i]);
+            }
+        }
+        if (s1_row) {
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    cq[c][e] = cs[c][e];
+                    n0[c][e] = c0v[c][e];
+                    n1[c][e] = c1v[c][e];
+                    n2[c][e] = c2v[c][e];
+                    pz0[c][e] = pz1[c][e];
+                    pz1[c][e] = c5v[c][e];
+                }
+            }
+            hl = hl_new;
+            hr = hr_new;
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <typename S, int CH, bool FULL, bool TILED>
 __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1) update2_slab(SlabParams<S> P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    slab_body<S, CH, FULL>(P, blockIdx.x, smem);
+    if constexpr (TILED)
+        slab_body_tiled<S, CH, FULL>(P, blockIdx.x, smem);
+    else
+        slab_body<S, CH, FULL>(P, blockIdx.x, smem);
 }
 
 // Batched ensembles: CTA j sweeps CTA j - cta_first[i] of lattice
@@ -549,6 +850,8 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
         P.nslab = L.plan.nslab;
         P.zc = L.plan.zc;
         P.nseg = L.plan.nseg;
+        P.ntile = 1;
+        P.tx = P.nx;
         P.err = L.b.err;
         slab_body<S, CH, FULL>(P, j - cta_first[i], smem);
     }
@@ -626,42 +929,70 @@ int chunks_for(int V, int mode) {
     return two_fit ? 2 : 1;
 }
 
+// Tile width for ntile x-tiles of a row of nx cells (multiple of 16 cells,
+// the last tile possibly narrower; ntile = 1: the whole row).
+inline int tile_width(int nx, int ntile) { return ntile <= 1 ? nx : ((nx + ntile - 1) / ntile + 15) / 16 * 16; }
+
+template <typename S, int CH, bool TILED>
+cudaError_t set_smem_attr(bool full, int smem_max) {
+    return full ? cudaFuncSetAttribute(update2_slab<S, CH, true, TILED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_max)
+                : cudaFuncSetAttribute(update2_slab<S, CH, false, TILED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_max);
+}
+
 // Slab height H (rows <= smem and thread limits; `want` > 0 asks for one)
-// and the z-chunk count minimising the estimated time, one CTA per SM: for
-// FP32 waves x planes per CTA x rows moved per plane (H + 2 read, H written);
-// for FP16 storage, whose planes cost a CTA mostly a fixed latency, waves x
-// planes.  Among heights within 5 % of the best estimate the tallest is taken.
+// and the z-chunk count minimising the estimated time, one CTA per SM, for
+// rows split into `ntile` x-tiles (1: whole rows).  FP32: waves x planes per
+// CTA x cells moved per plane (H + 2 staged rows read with their halo, H
+// written); FP16 storage, whose planes cost a CTA mostly a fixed latency:
+// waves x planes.  Among heights within 5 % of the best estimate the tallest
+// is taken.  *cost gets the estimate of the chosen plan, *hmax the tallest
+// slab that fits (either may be null).
 template <typename S, int CH>
-cudaError_t plan_ch(const Geometry &g, int want, int nseg, TwoStepPlan *pl) {
+cudaError_t plan_ch(const Geometry &g, int want, int ntile, TwoStepPlan *pl, double *cost, int *hmax) {
+    using R = typename Store<S>::R;
+    constexpr int W = Store<S>::W;
     int dev = 0, sms = 0, smem_max = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const int ny = g.n[1], nz = g.n[2];
-    const size_t per_row =
-        smem_per_row((size_t)g.n[0] * sizeof(S), (size_t)g.n[0] * sizeof(typename Store<S>::R), (size_t)g.n[0]);
-    const size_t per_row_all = per_row + (size_t)kRingPlanes * nseg * 2 * sizeof(typename Store<S>::R);
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const bool tiled = ntile > 1;
+    const int tx = tile_width(nx, ntile);
+    const int tiles = (nx + tx - 1) / tx;
+    if (tiled && (tiles < 2 || tx < 16)) return cudaErrorInvalidValue;
+    const int nseg = (tx / W + 32 * CH - 1) / (32 * CH);
+    if (tiled && nseg != 1) return cudaErrorInvalidValue;  // a tile row is one warp
+    const size_t per_row_all =
+        tiled ? smem_per_tile_row<S>(tx)
+              : smem_per_row((size_t)nx * sizeof(S), (size_t)nx * sizeof(R), (size_t)nx) +
+                    (size_t)kRingPlanes * nseg * 2 * sizeof(R);
     const size_t fixed = kStages * sizeof(uint64_t) + kStages * (size_t)kMaxRows + 16;
     int rows = (int)(((size_t)smem_max - fixed) / per_row_all);
     rows = std::min(rows, two_step_threads<S, CH>() / (32 * nseg));
+    rows = std::min(rows, kMaxRows);
     if (rows < 3) return cudaErrorInvalidValue;
+    if (hmax) *hmax = rows - 2;
     const int h_lo = want > 0 ? want : 1, h_hi = want > 0 ? want : rows - 2;
     if (h_hi > rows - 2) return cudaErrorInvalidValue;
+    const int hp = tiled ? halo_pop<S>() : 0;
     TwoStepPlan per_h[kMaxRows];
-    long long cost_h[kMaxRows], best = -1;
+    double cost_h[kMaxRows], best = -1;
     for (int H = h_lo; H <= h_hi; ++H) {
         const int nslab = (ny + H - 1) / H;
         cost_h[H] = -1;
         for (int C = 1; C <= nz; ++C) {
             const int zc = (nz + C - 1) / C;
             const int used = (nz + zc - 1) / zc;
-            const long long waves = ((long long)nslab * used + sms - 1) / sms;
-            // FP32: time follows the rows moved per plane; FP16 storage halves
+            const long long waves = ((long long)tiles * nslab * used + sms - 1) / sms;
+            // FP32: time follows the cells moved per plane; FP16 storage halves
             // the bytes and a plane's fixed latency dominates: count planes
-            const long long cost = sizeof(S) == 2 ? waves * (zc + 2) : waves * (zc + 2) * (2LL * H + 2);
-            if (cost_h[H] < 0 || cost < cost_h[H]) {
-                cost_h[H] = cost;
+            const double moved = (double)(H + 2) * (tx + 2 * hp) + (double)H * tx;
+            const double c = sizeof(S) == 2 ? (double)waves * (zc + 2) : (double)waves * (zc + 2) * moved;
+            if (cost_h[H] < 0 || c < cost_h[H]) {
+                cost_h[H] = c;
                 per_h[H].H = H;
                 per_h[H].nslab = nslab;
                 per_h[H].chunks = used;
@@ -671,33 +1002,61 @@ cudaError_t plan_ch(const Geometry &g, int want, int nseg, TwoStepPlan *pl) {
         if (best < 0 || cost_h[H] < best) best = cost_h[H];
     }
     for (int H = h_hi; H >= h_lo; --H)
-        if (cost_h[H] * 100 <= best * 105) {
+        if (cost_h[H] <= best * 1.05) {
             *pl = per_h[H];
+            if (cost) *cost = cost_h[H];
             break;
         }
     pl->nseg = nseg;
     pl->chunks_per_lane = CH;
+    pl->ntile = tiles;
+    pl->tx = tx;
     pl->threads = 32 * nseg * (pl->H + 2);
     pl->smem = per_row_all * (pl->H + 2) + fixed;
-    pl->full = (g.n[0] / Store<S>::W) % (32 * CH) == 0;
+    const int last = nx - (tiles - 1) * tx;  // cells of the last tile
+    pl->full = (tx / W) % (32 * CH) == 0 && (last / W) % (32 * CH) == 0;
     // the attribute belongs to the kernel, shared by every handle: allow the
     // device's whole opt-in shared memory, not just this plan's
-    return pl->full ? cudaFuncSetAttribute(update2_slab<S, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           smem_max)
-                    : cudaFuncSetAttribute(update2_slab<S, CH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           smem_max);
+    return tiled ? set_smem_attr<S, CH, true>(pl->full, smem_max) : set_smem_attr<S, CH, false>(pl->full, smem_max);
 }
 
 // Chunks per lane and segments per row for `mode` (1: automatic, 2: one
-// chunk, 3: two), then the slab plan.
+// chunk, 3: two) and x-tiles (0: automatic, 1: whole rows, n: n tiles), then
+// the slab plan.  Automatic tiles: whole rows wherever a whole-row slab fits
+// the shared memory (they are faster: at 512^3 FP32, 3-row whole-row slabs
+// take 1254 us per launch against 1410 us for 4 tiles of 14-row slabs);
+// rows too long for that take the cheapest estimate of 2 .. 16 tiles.
 template <typename S>
-cudaError_t plan_for(const Geometry &g, int want, int mode, TwoStepPlan *pl) {
-    const int V = row_vectors<S>(g);
-    const int ch = V ? chunks_for<S>(V, mode) : 0;
-    if (!ch) return cudaErrorInvalidValue;
-    if (ch == 1) return plan_ch<S, 1>(g, want, (V + 31) / 32, pl);
-    if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, (V + 63) / 64, pl);
-    return cudaErrorInvalidValue;
+cudaError_t plan_for(const Geometry &g, int want, int mode, int tiles, TwoStepPlan *pl) {
+    constexpr int W = Store<S>::W;
+    if (!row_vectors<S>(g)) return cudaErrorInvalidValue;
+    auto one = [&](int nt, TwoStepPlan *out, double *cost) -> cudaError_t {
+        const int tx = tile_width(g.n[0], nt);
+        if (nt > 1 && (g.n[0] + tx - 1) / tx < 2) return cudaErrorInvalidValue;
+        // a tile row is one warp: two chunks per lane where one does not cover it
+        const int ch = (nt > 1 && mode == 1 && tx / W > 32) ? (Store<S>::W * 2 <= 8 ? 2 : 0) : chunks_for<S>(tx / W, mode);
+        if (!ch) return cudaErrorInvalidValue;
+        if (ch == 1) return plan_ch<S, 1>(g, want, nt, out, cost, nullptr);
+        if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, nt, out, cost, nullptr);
+        return cudaErrorInvalidValue;
+    };
+    if (tiles >= 1) return one(tiles, pl, nullptr);
+    const cudaError_t e_whole = one(1, pl, nullptr);
+    if (e_whole == cudaSuccess) return e_whole;
+    TwoStepPlan best;
+    double best_cost = -1;
+    for (int nt : {2, 4, 8, 16}) {
+        TwoStepPlan c;
+        double cost = 0;
+        if (one(nt, &c, &cost) != cudaSuccess) continue;
+        if (best_cost < 0 || cost < best_cost) {
+            best = c;
+            best_cost = cost;
+        }
+    }
+    if (best_cost < 0) return e_whole;
+    *pl = best;
+    return cudaSuccess;
 }
 
 // The sampling kernel runs in 128-thread blocks so that one fits on an SM
@@ -721,6 +1080,8 @@ SlabParams<S> slab_params(const Geometry &g, const Buffers &b, const TwoStepPlan
     P.nslab = pl.nslab;
     P.zc = pl.zc;
     P.nseg = pl.nseg;
+    P.ntile = pl.ntile;
+    P.tx = pl.tx;
     P.err = err;
     return P;
 }
@@ -744,8 +1105,9 @@ cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl
         if (e == cudaSuccess && fork) e = cudaEventRecord(side.join, side.stream);
         if (e != cudaSuccess) return e;
     }
-    auto kernel = pl.full ? update2_slab<S, CH, true> : update2_slab<S, CH, false>;
-    kernel<<<pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(slab_params<S>(g, b, pl, src, err));
+    auto kernel = pl.ntile > 1 ? (pl.full ? update2_slab<S, CH, true, true> : update2_slab<S, CH, false, true>)
+                               : (pl.full ? update2_slab<S, CH, true, false> : update2_slab<S, CH, false, false>);
+    kernel<<<pl.ntile * pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(slab_params<S>(g, b, pl, src, err));
     e = cudaGetLastError();
     if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(s, side.join, 0);  // the next launch overwrites src
     return e;
@@ -766,17 +1128,17 @@ bool two_step_supported(const Geometry &g, Prec p) {
     if (g.dim != 3 || g.driven) return false;
     TwoStepPlan probe;
     switch (p) {
-        case Prec::F16: return row_vectors<__half>(g) > 0 && plan_for<__half>(g, 0, 1, &probe) == cudaSuccess;
-        case Prec::F32: return row_vectors<float>(g) > 0 && plan_for<float>(g, 0, 1, &probe) == cudaSuccess;
+        case Prec::F16: return row_vectors<__half>(g) > 0 && plan_for<__half>(g, 0, 1, 0, &probe) == cudaSuccess;
+        case Prec::F32: return row_vectors<float>(g) > 0 && plan_for<float>(g, 0, 1, 0, &probe) == cudaSuccess;
         default: return false;
     }
 }
 
-cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, TwoStepPlan *out) {
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, TwoStepPlan *out) {
     TwoStepPlan pl;
     if (g.dim != 3 || g.driven || (p != Prec::F16 && p != Prec::F32)) return cudaErrorInvalidValue;
-    cudaError_t e = p == Prec::F16 ? plan_for<__half>(g, slab_rows, mode, &pl)
-                                   : plan_for<float>(g, slab_rows, mode, &pl);
+    cudaError_t e = p == Prec::F16 ? plan_for<__half>(g, slab_rows, mode, tiles, &pl)
+                                   : plan_for<float>(g, slab_rows, mode, tiles, &pl);
     if (e == cudaSuccess) *out = pl;
     return e;
 }

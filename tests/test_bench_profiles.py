@@ -12,16 +12,13 @@ sys.path.insert(0, ROOT)
 
 import bench  # noqa: E402
 
-CELLS = 256 ** 3
-
-
-@pytest.mark.parametrize("steps_per_launch", [1, 2])
-def test_committed_profile_matches_current_kernel(steps_per_launch):
-    traffic = bench._traffic(bench._kernel_sha(steps_per_launch), steps_per_launch)
+@pytest.mark.parametrize("steps_per_launch,edge", [(1, 256), (2, 256), (2, 512)])
+def test_committed_profile_matches_current_kernel(steps_per_launch, edge):
+    traffic = bench._traffic(bench._kernel_sha(steps_per_launch), steps_per_launch, edge)
     assert traffic is not None, "kernel source changed since its profile was captured"
     # every population read and written once per launch, plus the class byte:
     # the measured bytes lie within a few per cent of 57 B per cell
-    algorithmic = 57.0 * CELLS
+    algorithmic = 57.0 * edge ** 3
     assert 0.9 * algorithmic < traffic < 1.1 * algorithmic
 
 

@@ -128,8 +128,8 @@ def test_sphere_512_full_size_short_run(wlb, precision, force_rtol):
     with wlb.Solver(prob) as s:
         info = s.info()
         assert info.steps_per_launch == 2
-        if precision == "f32":
-            assert info.two_step_segments == 2
+        if precision == "f32":  # whole rows: two warps of two chunks per row
+            assert info.two_step_tiles == 1 and info.two_step_segments == 2
         s.init()
         s.step(4, sample=False)
         s.step(4, sample=True)
@@ -344,18 +344,21 @@ def test_driven_cavity_steps_split_across_calls(wlb):
 
 # --- two unsampled steps per launch (slab temporal blocking) --------------------------
 
-def _two_step_outputs(wlb, prob, precision, settings, tail_steps=3, chunks_per_lane=0, segments=None):
+def _two_step_outputs(wlb, prob, precision, settings, tail_steps=3, chunks_per_lane=0, segments=None, tiles=1):
     """Force of the whole protocol, then `tail_steps` more unsampled steps
     (direct launches: one two-step launch and one single step for 3) and the
-    fields, for each (enable, slab_rows) in settings."""
+    fields, for each (enable, slab_rows) in settings; rows split into `tiles`
+    x-tiles (1: whole rows)."""
     out = []
     for enable, rows in settings:
         with wlb.Solver(prob, precision=precision) as s:
+            s.set_two_step_tiles(tiles)
             s.set_two_step(bool(enable), rows, chunks_per_lane)
             if enable:
                 info = s.info()
                 assert info.steps_per_launch == 2
                 assert info.two_step_rows == (rows or info.two_step_rows) and info.two_step_rows > 0
+                assert info.two_step_tiles == tiles
                 if segments is not None:
                     assert info.two_step_segments == segments
             F = s.run()
@@ -393,6 +396,65 @@ def test_two_step_is_bit_identical(wlb, shape, lam, precision, rows, cpl, segmen
         assert np.array_equal(out[0][0], o[0])
         assert np.array_equal(out[0][1], o[1])
         assert np.array_equal(out[0][2], o[2])
+
+
+@pytest.mark.parametrize("shape,lam,precision,tiles,rows,cpl", [
+    ((512, 24, 32), 16.0, "f32", 2, (0, 3, 7), 0),    # the 512-cell rows of the sweep lattice: 2 x 256
+    ((512, 22, 32), 16.0, "f32", 4, (0, 5, 13), 1),   # 4 tiles of one full warp of one chunk
+    ((400, 24, 32), 16.0, "f32", 2, (0, 3), 2),       # 208 + 192 cells: 52 and 48 of 64 vector slots
+    ((400, 21, 32), 16.0, "f32", 3, (0, 4), 2),       # 144 + 144 + 112 cells
+    ((96, 24, 32), 16.0, "f32", 2, (0, 5), 0),        # 48-cell tiles: both ends wrap around x
+    ((64, 24, 32), 16.0, "f32", 4, (0, 6), 0),        # 16-cell tiles, as narrow as the class-byte halo
+    ((512, 24, 32), 16.0, "f16", 2, (0, 9), 0),       # FP16 storage, 2 x 256 cells
+    ((256, 40, 32), 16.0, "f16", 2, (0, 6), 0),       # FP16, 16 of 32 lanes
+])
+def test_two_step_x_tiles_are_bit_identical(wlb, shape, lam, precision, tiles, rows, cpl):
+    """Rows split into x-tiles, one warp per tile row (each warp stages its
+    tile row plus 16 bytes of every array on either side, wrapped around x at
+    the row's ends, and computes the first step on the two cells outside it):
+    forces and fields equal one step per launch bit for bit, with full and
+    ragged tiles, several slab heights and both storage precisions."""
+    prob = workloads.problem(3, shape, 2, lam, 3.0, (shape[0] / 2 + 0.25, shape[1] / 2 - 0.5, lam / 8),
+                             cp=0.42, n_surface=200, n_periods=6, n_avg_periods=2)
+    out = _two_step_outputs(wlb, prob, precision, [(0, 0)] + [(1, r) for r in rows], chunks_per_lane=cpl,
+                            segments=1, tiles=tiles)
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0])
+        assert np.array_equal(out[0][1], o[1])
+        assert np.array_equal(out[0][2], o[2])
+
+
+def test_two_step_x_tiles_for_rows_too_long_for_whole_slabs(wlb):
+    """Whole rows wherever a whole-row slab fits (they are faster); 2048-cell
+    FP32 rows do not fit, so the automatic plan splits them into tiles of at
+    most one warp, and the result equals one step per launch bit for bit.
+    Tiles are rejected on 2D lattices."""
+    for nx, precision in ((512, "f32"), (256, "f32"), (512, "f16")):
+        prob = workloads.problem(3, (nx, 64, 32), 2, 16.0, 3.0, (nx / 2, 32.0, 2.0), cp=0.42, n_surface=16,
+                                 n_periods=2, n_avg_periods=1)
+        with wlb.Solver(prob, precision=precision) as s:
+            assert s.info().two_step_tiles == 1, (nx, precision)
+    wide = workloads.problem(3, (2048, 24, 32), 2, 16.0, 3.0, (1024.25, 11.5, 2.0), cp=0.42, n_surface=200,
+                             n_periods=4, n_avg_periods=2)
+    with wlb.Solver(wide) as s:
+        info = s.info()
+        assert info.steps_per_launch == 2 and info.two_step_tiles >= 8 and info.two_step_segments == 1
+    out = []
+    for enable in (False, True):
+        with wlb.Solver(wide) as s:
+            s.set_two_step(enable)
+            F = s.run()
+            s.step(3)
+            out.append((F,) + s.fields())
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+    p2 = workloads.problem(2, (128, 64), 1, 32.0, 4.0, (64.0, 4.0), cp=0.375, n_surface=16,
+                           n_periods=2, n_avg_periods=1)
+    with wlb.Solver(p2) as s:
+        s.set_two_step(True)
+        with pytest.raises(wlb.WlbError):
+            s.set_two_step_tiles(2)
+        assert s.info().steps_per_launch == 2
 
 
 @pytest.mark.parametrize("shape,lam,precision", [

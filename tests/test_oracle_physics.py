@@ -33,16 +33,7 @@ GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_v
 
 
 def _volume_ratio(dim, R, c0, cp, d=4.0):
-    from scipy.integrate import quad
-
-    def g(r):
-        c = cp + 0.5 * (c0 - cp) * (1 + math.tanh((r * r - R * R) / d))
-        return 1 - c0 * c0 / (c * c)
-
-    kap = c0 * c0 / (cp * cp)
-    if dim == 2:
-        return quad(lambda r: g(r) * 2 * math.pi * r, 0, R + 30, limit=400)[0] / ((1 - kap) * math.pi * R * R)
-    return quad(lambda r: g(r) * 4 * math.pi * r * r, 0, R + 30, limit=400)[0] / ((1 - kap) * 4 / 3 * math.pi * R ** 3)
+    return theory.volume_ratio(dim, R, c0, cp, d)
 
 
 def _cyl(cp, s0, R=8.0, lam=400.0, lateral=64, N=64):
