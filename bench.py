@@ -70,10 +70,11 @@ def _profile_name(steps_per_launch=1, edge=256):
     return "%s_d3q7_f32_%dcubed.md" % (kernel, edge)
 
 
-def _traffic(kernel_src_sha, steps_per_launch=1, edge=256):
-    """Per-launch DRAM bytes of the update kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", _profile_name(steps_per_launch, edge))
+def _traffic(kernel_src_sha, steps_per_launch=1, edge=256, name=None):
+    """Per-launch DRAM bytes of the update kernel from the committed ncu summary
+    (by default the FP32 update kernel's on an edge^3 lattice), if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", name or _profile_name(steps_per_launch, edge))
     try:
         text = open(path).read()
     except OSError:
@@ -92,12 +93,22 @@ def _traffic(kernel_src_sha, steps_per_launch=1, edge=256):
         return None
 
 
+HOST_MARKER = b"// ---------------------------------------------------------------- host side: plans and launches"
+
+
 def _kernel_sha(steps_per_launch=1):
-    """sha256 over the update kernel's source and the device header it includes."""
+    """sha256 over the update kernel's device code and the device header it
+    includes: wlb_step.cu whole, or wlb_two_step.cu up to its host-side part
+    (plans and launches, which a profile's counters do not depend on)."""
     csrc = os.path.join(ROOT, "paper_2404_02346_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("wlb_two_step.cu" if steps_per_launch == 2 else "wlb_step.cu", "wlb_kernels.cuh"):
-        h.update(open(os.path.join(csrc, name), "rb").read())
+    if steps_per_launch == 2:
+        text = open(os.path.join(csrc, "wlb_two_step.cu"), "rb").read()
+        cut = text.find(HOST_MARKER)
+        h.update(text if cut < 0 else text[:cut])
+    else:
+        h.update(open(os.path.join(csrc, "wlb_step.cu"), "rb").read())
+    h.update(open(os.path.join(csrc, "wlb_kernels.cuh"), "rb").read())
     return h.hexdigest()
 
 
@@ -431,11 +442,13 @@ def run_ensemble(args):
 
     B.build()
     if args.workload == "ensemble3d":
-        probs = workloads.ensemble_3d(seed=args.seed, precision=args.precision)
-        desc = "64 x 3D D3Q7 lattices, edge U{96,128,160}, lambda=edge/2, R~U[4,12], 1000 points, 25 periods"
+        count = args.count or 64
+        probs = workloads.ensemble_3d(seed=args.seed, count=count, precision=args.precision)
+        desc = "%d x 3D D3Q7 lattices, edge U{96,128,160}, lambda=edge/2, R~U[4,12], 1000 points, 25 periods" % count
     else:
-        probs = workloads.ensemble_2d(seed=args.seed, precision=args.precision)
-        desc = "512 x 2D D2Q5 192^2 lattices, lambda=96, R~U[4,12], 1000 points, 25 periods"
+        count = args.count or 512
+        probs = workloads.ensemble_2d(seed=args.seed, count=count, precision=args.precision)
+        desc = "%d x 2D D2Q5 192^2 lattices, lambda=96, R~U[4,12], 1000 points, 25 periods" % count
     stream = torch.cuda.Stream()
     batch = wlb.Batch(probs, stream=stream)
     tune = batch.autotune(steps_per_trial=16)
@@ -497,8 +510,13 @@ def run_ensemble(args):
         lu_per_force = info.lattice_updates / len(probs)
         cpu = dict(cpu, glups=cpu["value"], value=cpu["value"] * 1e9 / lu_per_force, unit="forces/s",
                    sample=cpu["sample"] + "; forces/s at the ensemble's mean %.3g LU per force" % lu_per_force)
+    # DRAM bytes of one two-step pass from the committed ncu summary (the
+    # 64-lattice FP32 ensemble only)
+    traffic = None
+    if args.workload == "ensemble3d" and args.precision == "f32" and len(probs) == 64 and spl == 2:
+        traffic = _traffic(_kernel_sha(2), name="batch_update2_d3q7_f32_ensemble64.md")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": ("batched two-step update" if spl == 2 else "batched update")
+                "traffic": traffic, "kernel": ("batched two-step update" if spl == 2 else "batched update")
                                           + " (%s storage), all lattices" % args.precision,
                 "bytes_per_cell_per_launch": bpu, "avg_launch_us": launch_ms * 1e3,
                 "peak_source": ("measured" if peaks and "hbm_gbs" in peaks else "fallback") + " hbm_gbs"}
@@ -779,6 +797,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=1500, help="surrogate training epochs")
     ap.add_argument("--queries", type=int, default=1 << 20, help="surrogate inference queries")
     ap.add_argument("--positions", type=int, default=16, help="sweep512: the first N of the 16 positions")
+    ap.add_argument("--count", type=int, default=0, help="ensembles: lattices (0: 64 in 3D, 512 in 2D)")
     ap.add_argument("--profile-nz", type=int, default=0, help="--profile: planes of a z-cut lattice (0: full)")
     args = ap.parse_args()
     if args.workload == "surrogate":

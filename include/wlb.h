@@ -315,12 +315,18 @@ wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, double force_ou
  *   wlb_batch_create           ws: NULL (library cudaMalloc) or a 256-byte
  *                              aligned device pointer of at least that size;
  *                              stream: cudaStream_t for all work.
- *   wlb_batch_autotune         times every launch shape (threads per block in
- *                              {128, 256} x blocks per SM in {2, 4, 8, 16}) for
- *                              steps_per_trial steps from a fresh setup and keeps
- *                              the fastest; the chosen shape is returned in
- *                              *best (may be NULL).  Leaves the lattices in an
- *                              advanced state; wlb_batch_run starts from setup.
+ *   wlb_batch_autotune         times candidates on the actual batch for
+ *                              steps_per_trial steps each (after a fresh setup)
+ *                              and keeps the fastest, returned in *best (may be
+ *                              NULL).  Two steps per launch (3D): every plan of
+ *                              z-chunk length {16, 32, 64, whole} x slab-height
+ *                              cap {tallest, 8, 5} x lane layout {one or two
+ *                              16-byte chunks per lane for wide rows, one for
+ *                              all}; 2D two steps: the one plan, timed; one
+ *                              step per launch: threads per block {128, 256} x
+ *                              blocks per SM {2, 4, 8, 16}.  Leaves the
+ *                              lattices in an advanced state; wlb_batch_run
+ *                              starts from setup.
  *   wlb_batch_run              setup, all steps, forces: forces_out is count x 3
  *                              host doubles (lattice order).  Synchronises.
  *                              WLB_ERR_UNSTABLE if any lattice's sums are not
@@ -333,6 +339,10 @@ typedef struct wlb_batch wlb_batch;
 typedef struct {
     int threads_per_block, blocks_per_sm;
     float ms_per_step;
+    int z_chunk;             /* two steps per launch (3D): z-chunk length target */
+    int slab_rows_cap;       /* ... slab-height cap (0: the tallest that fits)  */
+    int one_chunk_per_lane;  /* ... 1: one 16-byte chunk per lane everywhere   */
+    int plans_tried;         /* launch shapes or plans timed                    */
 } wlb_batch_tuning;
 typedef struct {
     int count;

@@ -48,15 +48,19 @@ def gelu_grad(z):
     return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
 
 
-def forward(theta, xn):
-    """xn: normalised inputs (B, 4).  Returns y (B,) and the cache."""
+def forward(theta, xn, act_round=None):
+    """xn: normalised inputs (B, 4).  Returns y (B,) and the cache.
+    act_round: None for FP64 activations, or a rounding applied to every
+    hidden activation (``bf16``: the network with BF16 activations, as the
+    surrogate's specification states them; products and sums stay FP64)."""
+    r = (lambda h: h) if act_round is None else act_round
     W1, b1, W2, b2, W3, b3, W4, b4 = unpack(theta)
     z1 = xn @ W1.T + b1
-    h1 = gelu(z1)
+    h1 = r(gelu(z1))
     z2 = h1 @ W2.T + b2
-    h2 = gelu(z2)
+    h2 = r(gelu(z2))
     z3 = h2 @ W3.T + b3
-    h3 = gelu(z3)
+    h3 = r(gelu(z3))
     y = (h3 @ W4.T + b4)[:, 0]
     return y, (xn, z1, h1, z2, h2, z3, h3)
 

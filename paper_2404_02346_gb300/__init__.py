@@ -64,7 +64,8 @@ class Info(ctypes.Structure):
 class BatchTuning(ctypes.Structure):
     """Mirror of ``wlb_batch_tuning``."""
     _fields_ = [("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("ms_per_step", ctypes.c_float)]
+                ("ms_per_step", ctypes.c_float), ("z_chunk", ctypes.c_int), ("slab_rows_cap", ctypes.c_int),
+                ("one_chunk_per_lane", ctypes.c_int), ("plans_tried", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -369,7 +370,8 @@ class Batch:
         self._bcheck(lib().wlb_batch_autotune(self._h, int(steps_per_trial), ctypes.byref(t)),
                      "wlb_batch_autotune")
         return {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm,
-                "ms_per_step": t.ms_per_step}
+                "ms_per_step": t.ms_per_step, "z_chunk": t.z_chunk, "slab_rows_cap": t.slab_rows_cap,
+                "one_chunk_per_lane": t.one_chunk_per_lane, "plans_tried": t.plans_tried}
 
     def run(self):
         F = np.zeros((self.count, 3))

@@ -293,6 +293,8 @@ struct wlb_batch {
     int two_ch = 1;                       // 2D: chunks per lane of the widest row
     int two_nx = 0;                       // 2D: widest row (staging slot size)
     int *d_cta_lat = nullptr, *d_cta_first = nullptr;
+    wlb::BatchTwoKnobs knobs;             // 3D: the plan's choices (wlb_batch_autotune)
+    int plan_gen = 0, graph_plan_gen = -1;  // the captured graph's plan
     char err[512] = {0};
 };
 
@@ -456,6 +458,59 @@ cudaError_t issue_steps(wlb_batch *b, int nsteps, int threads, int bps, cudaStre
     return cudaSuccess;
 }
 
+// Plan two steps per launch for every lattice with the knobs (3D; 2D has
+// one plan) and write the CTA (3D) or warp (2D) -> lattice table, each
+// lattice's first entry and, with upload_lats, the lattice descriptors that
+// carry the plans.  On failure nothing the launches read has changed.
+cudaError_t plan_two(wlb_batch *b, const wlb::BatchTwoKnobs &kn, bool upload_lats) {
+    const int count = b->count;
+    std::vector<BatchLat> lat = b->lat;
+    wlb::BatchTwoGroup groups[2];
+    int ngroups = 0, tasks2d = 0, two_ch = b->two_ch, two_nx = b->two_nx;
+    const bool planned = b->dim == 3 ? wlb::plan_batch_two_steps(b->prec, lat.data(), count, kn, groups, &ngroups)
+                                     : wlb::plan_batch2d_two_steps(b->prec, lat.data(), count, &tasks2d, &two_ch,
+                                                                   &two_nx);
+    if (!planned) return cudaErrorInvalidValue;
+    // CTA (3D) or warp (2D) -> lattice table, the lattices of each 3D
+    // lane-layout group together; first[i] = lattice i's first entry
+    std::vector<int> first(count + 1, 0), owner;
+    const int ngr = b->dim == 3 ? ngroups : 1;
+    int two_threads = 0;
+    for (int k = 0; k < ngr; ++k) {
+        const int begin = (int)owner.size();
+        for (int i = 0; i < count; ++i) {
+            if (b->dim == 3 && lat[i].plan.chunks_per_lane != groups[k].ch) continue;
+            const int n = lat[i].plan.nslab * lat[i].plan.chunks;
+            first[i] = (int)owner.size();
+            owner.insert(owner.end(), (size_t)n, i);
+        }
+        if (b->dim == 3) {
+            groups[k].cta_begin = begin;
+            groups[k].ctas = (int)owner.size() - begin;
+            two_threads = std::max(two_threads, groups[k].threads);
+        }
+    }
+    if (b->dim == 2) two_threads = lat[0].plan.threads;  // warps of a block
+    first[count] = (int)owner.size();
+    if ((long long)owner.size() > b->total_rows) return cudaErrorInvalidValue;  // table capacity
+    cudaError_t e = cudaMemcpy(b->d_cta_lat, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_cta_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && upload_lats)
+        e = cudaMemcpy(b->d_lats, lat.data(), sizeof(BatchLat) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    b->lat = lat;
+    for (int k = 0; k < 2; ++k) b->groups[k] = groups[k];
+    b->ngroups = ngroups;
+    b->two_ch = two_ch;
+    b->two_nx = two_nx;
+    b->two_threads = two_threads;
+    b->total_ctas = (int)owner.size();
+    b->knobs = kn;
+    ++b->plan_gen;
+    return cudaSuccess;
+}
+
 wlb_status batch_setup(wlb_batch *b) {
     for (int i = 0; i < b->count; ++i)
         BATCH_CUDA(b, wlb::launch_setup(b->lat[i].g, b->lat[i].b, b->prec, b->stream), "setup kernels");
@@ -613,39 +668,7 @@ wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws
     bool even = true;
     for (int i = 0; i < count && even; ++i)
         even = b->lat[i].n_steps % 2 == 0 && b->lat[i].window_begin % 2 == 0 && b->lat[i].period % 2 == 0;
-    int tasks2d = 0;
-    const bool planned =
-        even && (b->dim == 3 ? wlb::plan_batch_two_steps(b->prec, b->lat.data(), count, b->groups, &b->ngroups)
-                             : wlb::plan_batch2d_two_steps(b->prec, b->lat.data(), count, &tasks2d, &b->two_ch,
-                                                           &b->two_nx));
-    if (planned) {
-        // CTA (3D) or warp (2D) -> lattice table, the lattices of each 3D
-        // lane-layout group together; first[i] = lattice i's first entry
-        std::vector<int> first(count + 1, 0), owner;
-        const int ngr = b->dim == 3 ? b->ngroups : 1;
-        for (int k = 0; k < ngr; ++k) {
-            const int begin = (int)owner.size();
-            for (int i = 0; i < count; ++i) {
-                if (b->dim == 3 && b->lat[i].plan.chunks_per_lane != b->groups[k].ch) continue;
-                const int n = b->lat[i].plan.nslab * b->lat[i].plan.chunks;
-                first[i] = (int)owner.size();
-                owner.insert(owner.end(), (size_t)n, i);
-            }
-            if (b->dim == 3) {
-                b->groups[k].cta_begin = begin;
-                b->groups[k].ctas = (int)owner.size() - begin;
-                b->two_threads = std::max(b->two_threads, b->groups[k].threads);
-            }
-        }
-        if (b->dim == 2) b->two_threads = b->lat[0].plan.threads;  // warps of a block
-        first[count] = (int)owner.size();
-        b->total_ctas = (int)owner.size();
-        if (e == cudaSuccess)
-            e = cudaMemcpy(b->d_cta_lat, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(b->d_cta_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice);
-        b->two_ok = b->two = true;
-    }
+    if (e == cudaSuccess && even && plan_two(b, b->knobs, false) == cudaSuccess) b->two_ok = b->two = true;
     cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(b->d_lats, b->lat.data(), sizeof(BatchLat) * count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_pt_lat, pl.data(), sizeof(int) * pl.size(), cudaMemcpyHostToDevice);
@@ -668,23 +691,68 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
     cudaEvent_t e0, e1;
     BATCH_CUDA(b, cudaEventCreate(&e0), "event");
     BATCH_CUDA(b, cudaEventCreate(&e1), "event");
-    if (b->two) {  // the two-step launch has its own plan: time it, nothing to choose
+    if (b->two) {
+        // time one plan: a warm-up pair of steps, then steps from step 0 (all
+        // lattices active)
         const int steps = 2 * ((steps_per_trial + 1) / 2);
-        cudaError_t e = issue_steps(b, 2, b->threads, b->blocks_per_sm, b->stream);  // warm up
-        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(long long), b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-        if (e == cudaSuccess) e = issue_steps(b, steps, b->threads, b->blocks_per_sm, b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        auto trial = [&](float *ms) -> cudaError_t {
+            cudaError_t e = cudaMemsetAsync(b->d_step, 0, sizeof(long long), b->stream);
+            if (e == cudaSuccess) e = issue_steps(b, 2, b->threads, b->blocks_per_sm, b->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(long long), b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) e = issue_steps(b, steps, b->threads, b->blocks_per_sm, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+            return e;
+        };
+        float best_ms = 1e30f;
+        wlb::BatchTwoKnobs best_kn = b->knobs;
+        int tried = 0;
+        cudaError_t e = cudaSuccess;
+        if (b->dim == 3) {
+            // 3D: every plan of z-chunk length x slab-height cap x lane layout
+            // that fits, on the actual batch
+            const int zcs[] = {16, 32, 64, 1 << 20};
+            const int caps[] = {0, 8, 5};
+            for (int oc = 0; oc < 2 && e == cudaSuccess; ++oc)
+                for (int zc : zcs)
+                    for (int cap : caps) {
+                        wlb::BatchTwoKnobs kn;
+                        kn.zc_target = zc;
+                        kn.h_cap = cap;
+                        kn.one_chunk = oc;
+                        if (plan_two(b, kn, true) != cudaSuccess) {
+                            cudaGetLastError();
+                            continue;
+                        }
+                        float ms = 0;
+                        if ((e = trial(&ms)) != cudaSuccess) break;
+                        ++tried;
+                        if (ms < best_ms) {
+                            best_ms = ms;
+                            best_kn = kn;
+                        }
+                    }
+            if (e == cudaSuccess && (e = plan_two(b, best_kn, true)) != cudaSuccess) cudaGetLastError();
+        } else {
+            float ms = 0;  // 2D: one plan, timed
+            e = trial(&ms);
+            best_ms = ms;
+            tried = 1;
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (e != cudaSuccess) return bfail(b, WLB_ERR_CUDA, "autotune trial", e);
+        if (!tried) return bfail(b, WLB_ERR_CUDA, "autotune: no plan fits");
         if (best) {
             best->threads_per_block = b->two_threads;
             best->blocks_per_sm = 1;
-            best->ms_per_step = ms / steps;
+            best->ms_per_step = best_ms / steps;
+            best->z_chunk = b->dim == 3 ? best_kn.zc_target : 0;
+            best->slab_rows_cap = b->dim == 3 ? best_kn.h_cap : 0;
+            best->one_chunk_per_lane = b->dim == 3 ? best_kn.one_chunk : 0;
+            best->plans_tried = tried;
         }
         return WLB_OK;
     }
@@ -718,6 +786,8 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
         best->threads_per_block = bt;
         best->blocks_per_sm = bb;
         best->ms_per_step = best_ms / steps_per_trial;
+        best->z_chunk = best->slab_rows_cap = best->one_chunk_per_lane = 0;
+        best->plans_tried = 8;
     }
     return WLB_OK;
 }
@@ -727,7 +797,7 @@ wlb_status wlb_batch_run(wlb_batch *b, double *forces_out) {
     wlb_status st = batch_setup(b);
     if (st != WLB_OK) return st;
     if (!b->graph || b->graph_threads != b->threads || b->graph_bps != b->blocks_per_sm ||
-        b->graph_two != (int)b->two) {
+        b->graph_two != (int)b->two || b->graph_plan_gen != b->plan_gen) {
         if (b->graph) cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
         BATCH_CUDA(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -747,6 +817,7 @@ wlb_status wlb_batch_run(wlb_batch *b, double *forces_out) {
         b->graph_threads = b->threads;
         b->graph_bps = b->blocks_per_sm;
         b->graph_two = (int)b->two;
+        b->graph_plan_gen = b->plan_gen;
     }
     const long long full = b->max_steps / wlb::kGraphSteps, rest = b->max_steps % wlb::kGraphSteps;
     for (long long k = 0; k < full; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");

@@ -129,10 +129,18 @@ struct BatchTwoGroup {
     size_t smem = 0;         // its dynamic shared memory
     int cta_begin = 0, ctas = 0;  // its range of the CTA -> lattice table
 };
+// Choices of a batched two-step plan (the autotuner tries several):
+// z-chunks of about zc_target planes, slab heights capped at h_cap (0: the
+// tallest that fits), one_chunk: one 16-byte chunk per lane for every lattice
+// (rows over 32 vectors then take several warps) instead of two for wide rows.
+struct BatchTwoKnobs {
+    int zc_target = 32, h_cap = 0, one_chunk = 0;
+};
 // Plans every lattice (its plan lands in lats[i].plan) and fills up to two
 // groups (cta_begin / ctas are left to the caller); false if some lattice
 // cannot take two steps per launch.
-bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, BatchTwoGroup *groups, int *ngroups);
+bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, const BatchTwoKnobs &kn, BatchTwoGroup *groups,
+                          int *ngroups);
 // One launch of two steps for every active lattice: CTA j of the table works
 // on lattice cta_lat[j] (its CTA j - cta_first[lattice]); with points, a
 // sampling launch before it adds the sums of both steps.  The state at step t

@@ -911,6 +911,8 @@ __global__ void __launch_bounds__(256) batch_sample_two(const BatchLat *__restri
     }
 }
 
+// ---------------------------------------------------------------- host side: plans and launches
+
 // 16-byte vectors in a row, or 0 if a row is not a whole number of them or
 // its class bytes are not a whole number of 16-byte units (bulk copies).
 template <typename S>
@@ -1160,7 +1162,8 @@ namespace {
 // 32 vectors, two (FP32) for wider rows, so that a row of up to 64 vectors is
 // one warp and the slab can be taller; lattices are grouped by it.
 template <typename S, int CH>
-bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, BatchTwoGroup *grp) {
+bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, const BatchTwoKnobs &kn,
+                BatchTwoGroup *grp) {
     using R = typename Store<S>::R;
     const size_t fixed = kStages * sizeof(uint64_t) + kStages * (size_t)kMaxRows + 16;
     int t_max = 0;
@@ -1177,9 +1180,11 @@ bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, B
         if (rows < 3) return false;
         TwoStepPlan pl;
         pl.H = std::min(rows - 2, g.n[1]);
+        if (kn.h_cap > 0) pl.H = std::min(pl.H, kn.h_cap);
         pl.nslab = (g.n[1] + pl.H - 1) / pl.H;
-        // z-chunks of about 32 planes: many CTAs of similar work across lattices
-        pl.chunks = (g.n[2] + 31) / 32;
+        // z-chunks of about zc_target planes: many CTAs of similar work across lattices
+        const int zt = std::max(1, kn.zc_target);
+        pl.chunks = (g.n[2] + zt - 1) / zt;
         pl.zc = (g.n[2] + pl.chunks - 1) / pl.chunks;
         pl.chunks = (g.n[2] + pl.zc - 1) / pl.zc;
         pl.nseg = nseg;
@@ -1206,7 +1211,7 @@ bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, B
 }
 
 template <typename S>
-bool plan_batch_for(BatchLat *lats, int count, BatchTwoGroup *groups, int *ngroups) {
+bool plan_batch_for(BatchLat *lats, int count, const BatchTwoKnobs &kn, BatchTwoGroup *groups, int *ngroups) {
     int dev = 0, smem_max = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -1216,17 +1221,17 @@ bool plan_batch_for(BatchLat *lats, int count, BatchTwoGroup *groups, int *ngrou
         const Geometry &g = lats[i].g;
         const int V = row_vectors<S>(g);
         if (g.dim != 3 || g.driven || !V) return false;
-        if (Store<S>::W * 2 <= 8 && V > 32) two.push_back(i);
+        if (Store<S>::W * 2 <= 8 && V > 32 && !kn.one_chunk) two.push_back(i);
         else one.push_back(i);
     }
     int n = 0;
     if (!one.empty()) {
-        if (!plan_group<S, 1>(lats, one, smem_max, &groups[n])) return false;
+        if (!plan_group<S, 1>(lats, one, smem_max, kn, &groups[n])) return false;
         ++n;
     }
     if constexpr (Store<S>::W * 2 <= 8)
         if (!two.empty()) {
-            if (!plan_group<S, 2>(lats, two, smem_max, &groups[n])) return false;
+            if (!plan_group<S, 2>(lats, two, smem_max, kn, &groups[n])) return false;
             ++n;
         }
     *ngroups = n;
@@ -1263,10 +1268,11 @@ cudaError_t launch_batch_for(const BatchTwoGroup *groups, int ngroups, const Bat
 
 }  // namespace
 
-bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, BatchTwoGroup *groups, int *ngroups) {
+bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, const BatchTwoKnobs &kn, BatchTwoGroup *groups,
+                          int *ngroups) {
     switch (p) {
-        case Prec::F16: return plan_batch_for<__half>(lats, count, groups, ngroups);
-        case Prec::F32: return plan_batch_for<float>(lats, count, groups, ngroups);
+        case Prec::F16: return plan_batch_for<__half>(lats, count, kn, groups, ngroups);
+        case Prec::F32: return plan_batch_for<float>(lats, count, kn, groups, ngroups);
         default: return false;
     }
 }

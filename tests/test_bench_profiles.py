@@ -22,6 +22,12 @@ def test_committed_profile_matches_current_kernel(steps_per_launch, edge):
     assert 0.9 * algorithmic < traffic < 1.1 * algorithmic
 
 
+def test_committed_ensemble_profile_matches_current_kernel():
+    traffic = bench._traffic(bench._kernel_sha(2), name="batch_update2_d3q7_f32_ensemble64.md")
+    assert traffic is not None, "kernel source changed since its profile was captured"
+    assert 0.95 * 7.9287e9 < traffic < 1.1 * 7.9287e9  # 57 B x 139.1 M cells per two-step pass
+
+
 def test_foreign_source_hash_gives_no_traffic():
     assert bench._traffic("0" * 64, 2) is None
     assert bench._traffic("0" * 64, 1) is None

@@ -123,6 +123,10 @@ def test_batch_two_steps_per_launch_bit_identical(wlb, precision):
         b.set_two_step(True)
         best = b.autotune(steps_per_trial=8)
         assert best["blocks_per_sm"] == 1 and best["ms_per_step"] > 0
+        # plans tried: z-chunk length x slab-height cap x lane layout, fastest kept
+        assert best["plans_tried"] > 4
+        assert best["z_chunk"] in (16, 32, 64, 1 << 20) and best["slab_rows_cap"] in (0, 8, 5)
+        assert best["one_chunk_per_lane"] in (0, 1)
         F2b = b.run()
     assert np.array_equal(F2, F1) and np.array_equal(F2, F2b)
     assert np.array_equal(F2[3], np.zeros(3))  # no averaging window

@@ -69,3 +69,24 @@ def test_surrogate_pipeline(wlb):
     q_rate = 5 * 65536 / (time.perf_counter() - t0)
     assert q_rate > 100 * lb_rate, (q_rate, lb_rate)
     sur.close()
+
+
+def test_surrogate_held_out_error_within_one_percent(wlb):
+    """The accuracy bar of the learned surrogate at reduced lattice size: after
+    training on 8192 lattice forces (seeded Latin hypercube of the box), at
+    least 99 % of 1024 held-out lattice runs are predicted within 1 % of the
+    force scale (the largest held-out |normalised force|)."""
+    from paper_2404_02346_gb300 import surrogate as S
+
+    train = workloads.surrogate_problems(8192, seed=21, **SMALL)
+    val = workloads.surrogate_problems(1024, seed=22, **SMALL)
+    t_train = S.lattice_targets(train)
+    t_val = S.lattice_targets(val)
+    sur = S.Surrogate(workloads.SURROGATE_BOX, batch_max=8192)
+    sur.fit([p["features"] for p in train], t_train, epochs=1000, batch=256, lr=2e-3, lr_final=2e-5)
+    y, _ = sur.predict([p["features"] for p in val])
+    err = np.abs(y.cpu().numpy() - t_val)
+    scale = float(np.abs(t_val).max())
+    frac = float(np.mean(err <= 0.01 * scale))
+    sur.close()
+    assert frac >= 0.99, (frac, float(err.max() / scale), float(np.sqrt(np.mean(err ** 2)) / scale))

@@ -53,3 +53,24 @@ def test_packed_layout():
     assert [p.shape for p in parts] == mlp.SHAPES
     assert np.array_equal(mlp.pack(parts), theta)
     assert mlp.SIZE == 256 * 4 + 256 + 2 * (256 * 256 + 256) + 256 + 1
+
+
+def test_bf16_activations_option():
+    """forward(..., act_round=bf16): every hidden activation is the BF16
+    rounding of the exact GELU of its FP64 pre-activation (which sees the
+    rounded activations of the layer below); without rounding it is the FP64
+    network, and the BF16 network's output stays within the rounding's reach."""
+    rng = np.random.default_rng(6)
+    theta = mlp.init(3)
+    x = rng.uniform(-1, 1, size=(64, 4))
+    y64, _ = mlp.forward(theta, x)
+    assert np.array_equal(mlp.forward(theta, x, act_round=None)[0], y64)
+    y16, (x0, z1, h1, z2, h2, z3, h3) = mlp.forward(theta, x, act_round=mlp.bf16)
+    W1, b1, W2, b2, W3, b3, W4, b4 = mlp.unpack(theta)
+    assert np.array_equal(h1, mlp.bf16(mlp.gelu(x @ W1.T + b1)))
+    assert np.array_equal(h2, mlp.bf16(mlp.gelu(h1 @ W2.T + b2)))
+    assert np.array_equal(h3, mlp.bf16(mlp.gelu(h2 @ W3.T + b3)))
+    assert np.array_equal(y16, (h3 @ W4.T + b4)[:, 0])
+    assert np.all(mlp.bf16(h3) == h3)
+    # each activation moves by at most 2^-9 of itself; the output by a few 1e-3
+    assert 0 < np.abs(y16 - y64).max() < 1e-2 * np.abs(y64).max()
