@@ -141,6 +141,7 @@ typedef struct {
     int two_step_rows;          /* slab height of the two-step kernel, 0 off    */
     int two_step_segments;      /* warps per lattice row (per x-tile) in it, 0 off */
     int two_step_tiles;         /* x-tiles per row in it (1: whole rows), 0 off */
+    int two_step_staging_warp;  /* 1: a dedicated warp stages its planes        */
 } wlb_info;
 
 /* Check a parameter set.  WLB_ERR_ARG for: unknown lattice or precision,
@@ -322,7 +323,8 @@ wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, double force_ou
  *                              z-chunk length {16, 32, 64, whole} x slab-height
  *                              cap {tallest, 8, 5} x lane layout {one or two
  *                              16-byte chunks per lane for wide rows, one for
- *                              all}; 2D two steps: the one plan, timed; one
+ *                              all} x staging {warp 0, a dedicated warp per
+ *                              CTA}; 2D two steps: the one plan, timed; one
  *                              step per launch: threads per block {128, 256} x
  *                              blocks per SM {2, 4, 8, 16}.  Leaves the
  *                              lattices in an advanced state; wlb_batch_run
@@ -343,6 +345,8 @@ typedef struct {
     int slab_rows_cap;       /* ... slab-height cap (0: the tallest that fits)  */
     int one_chunk_per_lane;  /* ... 1: one 16-byte chunk per lane everywhere   */
     int plans_tried;         /* launch shapes or plans timed                    */
+    int staging_warp;        /* two steps per launch (3D): 1 = a dedicated warp
+                                per CTA stages the planes                       */
 } wlb_batch_tuning;
 typedef struct {
     int count;
@@ -486,6 +490,17 @@ wlb_status wlb_set_two_step(wlb_handle *h, int enable, int slab_rows);
  * 2D lattice (tiles > 1).  The paper has no counterpart: it changes how the
  * same update is scheduled, not what it computes. */
 wlb_status wlb_set_two_step_tiles(wlb_handle *h, int tiles);
+
+/* Who stages the planes of the two-step kernel with whole rows (3D): the
+ * bulk copies of a plane are issued once the plane barrier has passed, by
+ * one warp.  staging: 0 lets the library choose, 1 warp 0 (which also
+ * computes its row, so the next barrier waits for both), 2 a dedicated
+ * extra warp that only stages (one fewer slab row may fit the thread
+ * limit).  Bit-identical either way.  Applies to the current and later
+ * wlb_set_two_step settings; x-tiles stage per warp and ignore it.
+ * WLB_ERR_STATE while two steps per launch is off; WLB_ERR_ARG if the plan
+ * does not fit (setting unchanged) or on a 2D lattice (staging 2). */
+wlb_status wlb_set_two_step_staging(wlb_handle *h, int staging);
 
 /* Release the handle, its graphs, streams and any memory it allocated. */
 wlb_status wlb_destroy(wlb_handle *h);

@@ -58,6 +58,7 @@ class Info(ctypes.Structure):
         ("two_step_rows", ctypes.c_int),
         ("two_step_segments", ctypes.c_int),
         ("two_step_tiles", ctypes.c_int),
+        ("two_step_staging_warp", ctypes.c_int),
     ]
 
 
@@ -65,7 +66,8 @@ class BatchTuning(ctypes.Structure):
     """Mirror of ``wlb_batch_tuning``."""
     _fields_ = [("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("ms_per_step", ctypes.c_float), ("z_chunk", ctypes.c_int), ("slab_rows_cap", ctypes.c_int),
-                ("one_chunk_per_lane", ctypes.c_int), ("plans_tried", ctypes.c_int)]
+                ("one_chunk_per_lane", ctypes.c_int), ("plans_tried", ctypes.c_int),
+                ("staging_warp", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -102,6 +104,7 @@ _SIGNATURES = {
     "wlb_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(Info)]),
     "wlb_set_two_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "wlb_set_two_step_tiles": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "wlb_set_two_step_staging": (ctypes.c_int, [_VP, ctypes.c_int]),
     "wlb_destroy": (ctypes.c_int, [_VP]),
     "wlb_average_noalloc": (ctypes.c_int, [_VP, ctypes.c_longlong, _DP]),
     "wlb_batch_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int,
@@ -256,6 +259,11 @@ class Solver:
         lets the library choose, 1 keeps whole rows, n splits rows in n."""
         _check(lib().wlb_set_two_step_tiles(self._h, int(tiles)), self._h, "wlb_set_two_step_tiles")
 
+    def set_two_step_staging(self, staging=0):
+        """Who stages the two-step kernel's planes (wlb_set_two_step_staging):
+        0 automatic, 1 warp 0, 2 a dedicated warp."""
+        _check(lib().wlb_set_two_step_staging(self._h, int(staging)), self._h, "wlb_set_two_step_staging")
+
     def step(self, n, sample=False):
         _check(lib().wlb_step(self._h, int(n), 1 if sample else 0), self._h, "wlb_step")
 
@@ -371,7 +379,8 @@ class Batch:
                      "wlb_batch_autotune")
         return {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm,
                 "ms_per_step": t.ms_per_step, "z_chunk": t.z_chunk, "slab_rows_cap": t.slab_rows_cap,
-                "one_chunk_per_lane": t.one_chunk_per_lane, "plans_tried": t.plans_tried}
+                "one_chunk_per_lane": t.one_chunk_per_lane, "plans_tried": t.plans_tried,
+                "staging_warp": t.staging_warp}
 
     def run(self):
         F = np.zeros((self.count, 3))

@@ -715,6 +715,7 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
             // that fits, on the actual batch
             const int zcs[] = {16, 32, 64, 1 << 20};
             const int caps[] = {0, 8, 5};
+            for (int sw = 0; sw < 2 && e == cudaSuccess; ++sw)
             for (int oc = 0; oc < 2 && e == cudaSuccess; ++oc)
                 for (int zc : zcs)
                     for (int cap : caps) {
@@ -722,6 +723,7 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
                         kn.zc_target = zc;
                         kn.h_cap = cap;
                         kn.one_chunk = oc;
+                        kn.staging_warp = sw;
                         if (plan_two(b, kn, true) != cudaSuccess) {
                             cudaGetLastError();
                             continue;
@@ -752,6 +754,7 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
             best->z_chunk = b->dim == 3 ? best_kn.zc_target : 0;
             best->slab_rows_cap = b->dim == 3 ? best_kn.h_cap : 0;
             best->one_chunk_per_lane = b->dim == 3 ? best_kn.one_chunk : 0;
+            best->staging_warp = b->dim == 3 ? best_kn.staging_warp : 0;
             best->plans_tried = tried;
         }
         return WLB_OK;
@@ -786,7 +789,7 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
         best->threads_per_block = bt;
         best->blocks_per_sm = bb;
         best->ms_per_step = best_ms / steps_per_trial;
-        best->z_chunk = best->slab_rows_cap = best->one_chunk_per_lane = 0;
+        best->z_chunk = best->slab_rows_cap = best->one_chunk_per_lane = best->staging_warp = 0;
         best->plans_tried = 8;
     }
     return WLB_OK;

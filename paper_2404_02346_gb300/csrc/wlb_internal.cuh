@@ -89,15 +89,18 @@ bool update_is_vectorised(const Geometry &g, Prec p);
 struct TwoStepPlan {
     int H = 0, nslab = 0, chunks = 0, zc = 0, nseg = 0, chunks_per_lane = 0, threads = 0;
     int ntile = 1, tx = 0;  // x-tiles per row and their width (1: whole rows)
+    int producer = 0;       // whole rows: 1 = a dedicated warp stages the planes
     bool full = false;      // every segment a full warp (no idle lanes)
     size_t smem = 0;
 };
 bool two_step_supported(const Geometry &g, Prec p);
 // slab_rows: 0 picks H; otherwise that H.  mode: 1 automatic, 2 one 16-byte
 // chunk per lane, 3 two.  tiles: 0 automatic, 1 whole rows, n >= 2 n x-tiles
-// per row.  Also opts the kernel into the shared memory it needs on the
-// current device.
-cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, TwoStepPlan *out);
+// per row.  staging: 0 automatic, 1 warp 0 stages planes besides computing,
+// 2 a dedicated staging warp.  Also opts the kernel into the shared memory it
+// needs on the current device.
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, int staging,
+                           TwoStepPlan *out);
 // Side stream and events that let the sampling kernel of a sampled two-step
 // launch run beside the update (fork before, join after).
 struct SideStream {
@@ -132,9 +135,10 @@ struct BatchTwoGroup {
 // Choices of a batched two-step plan (the autotuner tries several):
 // z-chunks of about zc_target planes, slab heights capped at h_cap (0: the
 // tallest that fits), one_chunk: one 16-byte chunk per lane for every lattice
-// (rows over 32 vectors then take several warps) instead of two for wide rows.
+// (rows over 32 vectors then take several warps) instead of two for wide rows;
+// staging_warp: a dedicated warp per CTA stages the planes.
 struct BatchTwoKnobs {
-    int zc_target = 32, h_cap = 0, one_chunk = 0;
+    int zc_target = 32, h_cap = 0, one_chunk = 0, staging_warp = 0;
 };
 // Plans every lattice (its plan lands in lats[i].plan) and fills up to two
 // groups (cta_begin / ctas are left to the caller); false if some lattice

@@ -282,6 +282,7 @@ struct SlabParams {
     typename Store<S>::R c0sq, cpsq;
     int H, nslab, zc, nseg;  // plan
     int ntile, tx;           // x-tiles per row and their width in cells (ntile = 1: whole rows)
+    int producer;            // whole rows: 1 = warp nseg * (H + 2) only stages planes, 0 = warp 0 also computes
     int *err;
 };
 
@@ -320,6 +321,7 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
     if (za >= zb) return;            // whole block: empty chunk
     const int L = zb - za + 2;       // S1 planes za-1 .. zb
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int issuer = P.producer ? nseg * rmax : 0;  // the warp that stages planes (a dedicated one computes nothing)
     const uint32_t row_bytes = (uint32_t)(nx * sizeof(S)), c2_bytes = (uint32_t)(nx * sizeof(R));
 
     if (threadIdx.x == 0) {
@@ -336,7 +338,7 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
         return band_rows[(long long)p * ny + (y0 - 1 + lane + ny) % ny];
     };
     // Stage the rows of S1 plane index k (plane za-1+k) into stage k % 2:
-    // lane i < 8 of warp 0 copies population i (i = 7: the class bytes) for
+    // lane i < 8 of the issuing warp copies population i (i = 7: the class bytes) for
     // the rs rows, one bulk copy per run of rows that is contiguous in memory
     // (two where the slab's halo wraps around y); lane 8 + r copies the c^2 row
     // of S1 row r when that row holds band cells (flag).
@@ -371,15 +373,16 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
             bulk_load(c2s + ((size_t)buf * rmax + r) * rowel, c2f + row0 * nx, c2_bytes, &bar[buf]);
         }
     };
-    int flag_next = 0;  // warp 0: band flag of plane index k + kStages, for the issue in iteration k
-    if (warp == 0) {
+    int flag_next = 0;  // issuing warp: band flag of plane index k + kStages, for the issue in iteration k
+    if (warp == issuer) {
         for (int j = 0; j < kStages && j < L; ++j) issue(j, band_flag(j));
         flag_next = band_flag(kStages);
     }
     __syncthreads();  // row flags of the first stages
 
     // warp -> S1 row `row` of the slab (y0-1+row) and segment `seg` of it
-    // (cells xs .. xs + 32*W*CH - 1)
+    // (cells xs .. xs + 32*W*CH - 1); a dedicated staging warp gets row rmax
+    // and computes nothing
     const int row = warp / nseg, seg = warp % nseg;
     const int xs = seg * 32 * W * CH;
     const int vg = FULL ? 32 * CH : min(32 * CH, nx / W - seg * 32 * CH);  // vectors of this segment
@@ -482,7 +485,7 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
             failed = 1;
             break;
         }
-        if (warp == 0 && k + kStages < L) {
+        if (warp == issuer && k + kStages < L) {
             issue(k + kStages, flag_next);
             flag_next = band_flag(k + kStages + 1);  // used in the next iteration
         }
@@ -852,6 +855,7 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
         P.nseg = L.plan.nseg;
         P.ntile = 1;
         P.tx = P.nx;
+        P.producer = L.plan.producer;
         P.err = L.b.err;
         slab_body<S, CH, FULL>(P, j - cta_first[i], smem);
     }
@@ -952,7 +956,7 @@ cudaError_t set_smem_attr(bool full, int smem_max) {
 // is taken.  *cost gets the estimate of the chosen plan, *hmax the tallest
 // slab that fits (either may be null).
 template <typename S, int CH>
-cudaError_t plan_ch(const Geometry &g, int want, int ntile, TwoStepPlan *pl, double *cost, int *hmax) {
+cudaError_t plan_ch(const Geometry &g, int want, int ntile, int staging, TwoStepPlan *pl, double *cost, int *hmax) {
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
     int dev = 0, sms = 0, smem_max = 0;
@@ -967,13 +971,15 @@ cudaError_t plan_ch(const Geometry &g, int want, int ntile, TwoStepPlan *pl, dou
     if (tiled && (tiles < 2 || tx < 16)) return cudaErrorInvalidValue;
     const int nseg = (tx / W + 32 * CH - 1) / (32 * CH);
     if (tiled && nseg != 1) return cudaErrorInvalidValue;  // a tile row is one warp
+    // whole rows: a dedicated staging warp on request (tiles stage per warp)
+    const int producer = !tiled && staging == 2 ? 1 : 0;
     const size_t per_row_all =
         tiled ? smem_per_tile_row<S>(tx)
               : smem_per_row((size_t)nx * sizeof(S), (size_t)nx * sizeof(R), (size_t)nx) +
                     (size_t)kRingPlanes * nseg * 2 * sizeof(R);
     const size_t fixed = kStages * sizeof(uint64_t) + kStages * (size_t)kMaxRows + 16;
     int rows = (int)(((size_t)smem_max - fixed) / per_row_all);
-    rows = std::min(rows, two_step_threads<S, CH>() / (32 * nseg));
+    rows = std::min(rows, (two_step_threads<S, CH>() / 32 - producer) / nseg);
     rows = std::min(rows, kMaxRows);
     if (rows < 3) return cudaErrorInvalidValue;
     if (hmax) *hmax = rows - 2;
@@ -1013,7 +1019,8 @@ cudaError_t plan_ch(const Geometry &g, int want, int ntile, TwoStepPlan *pl, dou
     pl->chunks_per_lane = CH;
     pl->ntile = tiles;
     pl->tx = tx;
-    pl->threads = 32 * nseg * (pl->H + 2);
+    pl->producer = producer;
+    pl->threads = 32 * (nseg * (pl->H + 2) + producer);
     pl->smem = per_row_all * (pl->H + 2) + fixed;
     const int last = nx - (tiles - 1) * tx;  // cells of the last tile
     pl->full = (tx / W) % (32 * CH) == 0 && (last / W) % (32 * CH) == 0;
@@ -1029,7 +1036,7 @@ cudaError_t plan_ch(const Geometry &g, int want, int ntile, TwoStepPlan *pl, dou
 // take 1254 us per launch against 1410 us for 4 tiles of 14-row slabs);
 // rows too long for that take the cheapest estimate of 2 .. 16 tiles.
 template <typename S>
-cudaError_t plan_for(const Geometry &g, int want, int mode, int tiles, TwoStepPlan *pl) {
+cudaError_t plan_for(const Geometry &g, int want, int mode, int tiles, int staging, TwoStepPlan *pl) {
     constexpr int W = Store<S>::W;
     if (!row_vectors<S>(g)) return cudaErrorInvalidValue;
     auto one = [&](int nt, TwoStepPlan *out, double *cost) -> cudaError_t {
@@ -1038,13 +1045,30 @@ cudaError_t plan_for(const Geometry &g, int want, int mode, int tiles, TwoStepPl
         // a tile row is one warp: two chunks per lane where one does not cover it
         const int ch = (nt > 1 && mode == 1 && tx / W > 32) ? (Store<S>::W * 2 <= 8 ? 2 : 0) : chunks_for<S>(tx / W, mode);
         if (!ch) return cudaErrorInvalidValue;
-        if (ch == 1) return plan_ch<S, 1>(g, want, nt, out, cost, nullptr);
-        if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, nt, out, cost, nullptr);
+        if (ch == 1) return plan_ch<S, 1>(g, want, nt, staging, out, cost, nullptr);
+        if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, nt, staging, out, cost, nullptr);
         return cudaErrorInvalidValue;
     };
-    if (tiles >= 1) return one(tiles, pl, nullptr);
-    const cudaError_t e_whole = one(1, pl, nullptr);
-    if (e_whole == cudaSuccess) return e_whole;
+    if (tiles >= 1 && staging != 0) return one(tiles, pl, nullptr);
+    if (tiles > 1) return one(tiles, pl, nullptr);
+    // whole rows; a dedicated staging warp unless the thread limit then costs
+    // slab height worth more than 3 % of the recomputed halo rows (measured:
+    // 256^3 FP32 7 rows either way, 153.8 -> 149.7 us; 256^3 FP16 10 -> 9
+    // rows, 114.2 -> 104.9 us; 512^3 FP16 4 -> 3 rows, 953.6 -> 1027.6 us)
+    TwoStepPlan p0, p1;
+    cudaError_t e_whole = one(1, &p0, nullptr);
+    if (e_whole == cudaSuccess && staging == 0) {
+        staging = 2;
+        if (one(1, &p1, nullptr) == cudaSuccess &&
+            (double)(p1.H + 2) / p1.H <= 1.03 * (double)(p0.H + 2) / p0.H)
+            p0 = p1;
+        staging = 0;
+    }
+    if (e_whole == cudaSuccess) {
+        *pl = p0;
+        return e_whole;
+    }
+    if (tiles == 1) return e_whole;
     TwoStepPlan best;
     double best_cost = -1;
     for (int nt : {2, 4, 8, 16}) {
@@ -1084,6 +1108,7 @@ SlabParams<S> slab_params(const Geometry &g, const Buffers &b, const TwoStepPlan
     P.nseg = pl.nseg;
     P.ntile = pl.ntile;
     P.tx = pl.tx;
+    P.producer = pl.producer;
     P.err = err;
     return P;
 }
@@ -1130,17 +1155,18 @@ bool two_step_supported(const Geometry &g, Prec p) {
     if (g.dim != 3 || g.driven) return false;
     TwoStepPlan probe;
     switch (p) {
-        case Prec::F16: return row_vectors<__half>(g) > 0 && plan_for<__half>(g, 0, 1, 0, &probe) == cudaSuccess;
-        case Prec::F32: return row_vectors<float>(g) > 0 && plan_for<float>(g, 0, 1, 0, &probe) == cudaSuccess;
+        case Prec::F16: return row_vectors<__half>(g) > 0 && plan_for<__half>(g, 0, 1, 0, 0, &probe) == cudaSuccess;
+        case Prec::F32: return row_vectors<float>(g) > 0 && plan_for<float>(g, 0, 1, 0, 0, &probe) == cudaSuccess;
         default: return false;
     }
 }
 
-cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, TwoStepPlan *out) {
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, int staging,
+                           TwoStepPlan *out) {
     TwoStepPlan pl;
     if (g.dim != 3 || g.driven || (p != Prec::F16 && p != Prec::F32)) return cudaErrorInvalidValue;
-    cudaError_t e = p == Prec::F16 ? plan_for<__half>(g, slab_rows, mode, tiles, &pl)
-                                   : plan_for<float>(g, slab_rows, mode, tiles, &pl);
+    cudaError_t e = p == Prec::F16 ? plan_for<__half>(g, slab_rows, mode, tiles, staging, &pl)
+                                   : plan_for<float>(g, slab_rows, mode, tiles, staging, &pl);
     if (e == cudaSuccess) *out = pl;
     return e;
 }
@@ -1179,6 +1205,9 @@ bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, c
         rows = std::min(rows, two_step_threads<S, CH>() / (32 * nseg));
         if (rows < 3) return false;
         TwoStepPlan pl;
+        pl.producer = kn.staging_warp ? 1 : 0;
+        if (pl.producer) rows = std::min(rows, (two_step_threads<S, CH>() / 32 - 1) / nseg);
+        if (rows < 3) return false;
         pl.H = std::min(rows - 2, g.n[1]);
         if (kn.h_cap > 0) pl.H = std::min(pl.H, kn.h_cap);
         pl.nslab = (g.n[1] + pl.H - 1) / pl.H;
@@ -1189,7 +1218,7 @@ bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, c
         pl.chunks = (g.n[2] + pl.zc - 1) / pl.zc;
         pl.nseg = nseg;
         pl.chunks_per_lane = CH;
-        pl.threads = 32 * nseg * (pl.H + 2);
+        pl.threads = 32 * (nseg * (pl.H + 2) + pl.producer);
         pl.smem = per_row * (pl.H + 2) + fixed;
         pl.full = V % (32 * CH) == 0;
         lats[i].plan = pl;

@@ -126,7 +126,7 @@ def test_batch_two_steps_per_launch_bit_identical(wlb, precision):
         # plans tried: z-chunk length x slab-height cap x lane layout, fastest kept
         assert best["plans_tried"] > 4
         assert best["z_chunk"] in (16, 32, 64, 1 << 20) and best["slab_rows_cap"] in (0, 8, 5)
-        assert best["one_chunk_per_lane"] in (0, 1)
+        assert best["one_chunk_per_lane"] in (0, 1) and best["staging_warp"] in (0, 1)
         F2b = b.run()
     assert np.array_equal(F2, F1) and np.array_equal(F2, F2b)
     assert np.array_equal(F2[3], np.zeros(3))  # no averaging window

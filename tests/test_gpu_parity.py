@@ -424,6 +424,35 @@ def test_two_step_x_tiles_are_bit_identical(wlb, shape, lam, precision, tiles, r
         assert np.array_equal(out[0][2], o[2])
 
 
+@pytest.mark.parametrize("staging", [1, 2])
+@pytest.mark.parametrize("shape,lam,precision,rows", [
+    ((256, 24, 32), 16.0, "f32", (0, 3)),    # one warp per row
+    ((512, 24, 32), 16.0, "f32", (0, 2)),    # two warps per row
+    ((160, 24, 32), 16.0, "f32", (0, 4)),    # ragged: 40 of 64 vector slots
+    ((256, 40, 32), 16.0, "f16", (0, 5)),    # FP16 storage
+])
+def test_two_step_staging_warp_is_bit_identical(wlb, shape, lam, precision, rows, staging):
+    """The planes staged by warp 0 between its own rows (1) or by an extra
+    warp that computes nothing (2): forces and fields equal one step per
+    launch bit for bit."""
+    prob = workloads.problem(3, shape, 2, lam, 3.0, (shape[0] / 2 + 0.25, shape[1] / 2 - 0.5, lam / 8),
+                             cp=0.42, n_surface=200, n_periods=6, n_avg_periods=2)
+    out = []
+    for enable, r in [(0, 0)] + [(1, r) for r in rows]:
+        with wlb.Solver(prob, precision=precision) as s:
+            s.set_two_step_staging(staging)
+            s.set_two_step(bool(enable), r)
+            if enable:
+                info = s.info()
+                assert info.steps_per_launch == 2 and info.two_step_staging_warp == staging - 1
+            F = s.run()
+            s.step(3)
+            out.append((F,) + s.fields())
+    for o in out[1:]:
+        for a, b in zip(out[0], o):
+            assert np.array_equal(a, b)
+
+
 def test_two_step_x_tiles_for_rows_too_long_for_whole_slabs(wlb):
     """Whole rows wherever a whole-row slab fits (they are faster); 2048-cell
     FP32 rows do not fit, so the automatic plan splits them into tiles of at
