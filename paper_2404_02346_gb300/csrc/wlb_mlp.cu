@@ -173,13 +173,14 @@ __device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsig
 }
 
 // The GELU above for two pre-activations at once, as the epilogue of every
-// forward path evaluates it: the products and sums on packed pairs (each lane
-// rounded as the scalar instruction would round it), |z| and the two MUFU
-// steps per lane, about 9 instructions per value against 14 for the same
-// steps one value at a time.  (Written one value at a time with the same
-// operations, the result differed from this one in the last place for about
-// one negative input in 30; every path calls this one, so the paths agree bit
-// for bit.)
+// forward path evaluates it: the products and sums on packed pairs, |z| and
+// the two MUFU steps per lane, about 9 instructions per value against 14 one
+// value at a time.  Each packed instruction alone rounds every lane as its
+// scalar form does, but the compiler contracts some packed products into the
+// following packed sum (a fused multiply-add, one rounding fewer) although
+// the instructions carry .rn; so the result can differ from the scalar
+// sequence in the last place (about one negative input in 30), well inside
+// the A&S bound.  Every path calls this one, so the paths agree bit for bit.
 __device__ __forceinline__ void gelu2(float z0, float z1, float &g0, float &g1) {
     const unsigned long long z = f2_pack(z0, z1);
     const unsigned long long az = f2_pack(fabsf(z0), fabsf(z1));
