@@ -142,6 +142,8 @@ typedef struct {
     int two_step_segments;      /* warps per lattice row (per x-tile) in it, 0 off */
     int two_step_tiles;         /* x-tiles per row in it (1: whole rows), 0 off */
     int two_step_staging_warp;  /* 1: a dedicated warp stages its planes        */
+    int two_step_c2_staged;     /* 3D whole rows: 1 band rows' c^2 staged in
+                                   shared memory, 0 read from L2               */
 } wlb_info;
 
 /* Check a parameter set.  WLB_ERR_ARG for: unknown lattice or precision,
@@ -501,6 +503,20 @@ wlb_status wlb_set_two_step_tiles(wlb_handle *h, int tiles);
  * WLB_ERR_STATE while two steps per launch is off; WLB_ERR_ARG if the plan
  * does not fit (setting unchanged) or on a 2D lattice (staging 2). */
 wlb_status wlb_set_two_step_staging(wlb_handle *h, int staging);
+
+/* Where the two-step kernel with whole rows (3D) reads c^2 of rows that hold
+ * interface-band cells (Eq. 79's smooth profile; elsewhere c^2 follows from
+ * the cell class).  Staged in shared memory beside the populations, c^2
+ * takes slab height from long rows (512-cell FP32 rows: 3-row slabs with it,
+ * 4 without); otherwise the first step reads it from global memory, where
+ * the staging warp has prefetched the row into L2 two planes ahead.  c2: 0
+ * lets the library choose (staged wherever the slab height allows it), 1
+ * staged, 2 read from L2.  Bit-identical either way.  Applies to the current
+ * and later wlb_set_two_step settings; x-tiles always stage it.
+ * WLB_ERR_STATE while two steps per launch is off; WLB_ERR_ARG if the plan
+ * does not fit (setting unchanged) or on a 2D lattice (c2 != 0).  The paper
+ * has no counterpart: it moves the same values through another memory. */
+wlb_status wlb_set_two_step_c2(wlb_handle *h, int c2);
 
 /* Release the handle, its graphs, streams and any memory it allocated. */
 wlb_status wlb_destroy(wlb_handle *h);

@@ -59,6 +59,7 @@ class Info(ctypes.Structure):
         ("two_step_segments", ctypes.c_int),
         ("two_step_tiles", ctypes.c_int),
         ("two_step_staging_warp", ctypes.c_int),
+        ("two_step_c2_staged", ctypes.c_int),
     ]
 
 
@@ -105,6 +106,7 @@ _SIGNATURES = {
     "wlb_set_two_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "wlb_set_two_step_tiles": (ctypes.c_int, [_VP, ctypes.c_int]),
     "wlb_set_two_step_staging": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "wlb_set_two_step_c2": (ctypes.c_int, [_VP, ctypes.c_int]),
     "wlb_destroy": (ctypes.c_int, [_VP]),
     "wlb_average_noalloc": (ctypes.c_int, [_VP, ctypes.c_longlong, _DP]),
     "wlb_batch_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int,
@@ -263,6 +265,11 @@ class Solver:
         """Who stages the two-step kernel's planes (wlb_set_two_step_staging):
         0 automatic, 1 warp 0, 2 a dedicated warp."""
         _check(lib().wlb_set_two_step_staging(self._h, int(staging)), self._h, "wlb_set_two_step_staging")
+
+    def set_two_step_c2(self, c2=0):
+        """Where the two-step kernel reads band rows' c^2 (wlb_set_two_step_c2):
+        0 automatic, 1 staged in shared memory, 2 from L2."""
+        _check(lib().wlb_set_two_step_c2(self._h, int(c2)), self._h, "wlb_set_two_step_c2")
 
     def step(self, n, sample=False):
         _check(lib().wlb_step(self._h, int(n), 1 if sample else 0), self._h, "wlb_step")

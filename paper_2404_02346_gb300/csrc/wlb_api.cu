@@ -148,15 +148,16 @@ cudaError_t two_steps(wlb_handle *h, int src, bool sampled, cudaStream_t s) {
 }
 
 // Whether, and with which plan, a handle can take two steps per launch.
-bool two_step_plan(const wlb_handle *h, int slab_rows, int mode, int tiles, int staging, wlb::TwoStepPlan *plan,
-                   cudaError_t *err) {
+bool two_step_plan(const wlb_handle *h, int slab_rows, int mode, int tiles, int staging, int c2,
+                   wlb::TwoStepPlan *plan, cudaError_t *err) {
     if (h->g.dim == 2) {
-        if (!wlb::two_step_2d_supported(h->g, h->prec) || slab_rows != 0 || tiles > 1 || staging == 2) return false;
+        if (!wlb::two_step_2d_supported(h->g, h->prec) || slab_rows != 0 || tiles > 1 || staging == 2 || c2 != 0)
+            return false;
         *err = wlb::plan_two_steps_2d(h->g, h->prec, plan);
         return true;
     }
     if (!wlb::two_step_supported(h->g, h->prec)) return false;
-    *err = wlb::plan_two_steps(h->g, h->prec, slab_rows, mode, tiles, staging, plan);
+    *err = wlb::plan_two_steps(h->g, h->prec, slab_rows, mode, tiles, staging, c2, plan);
     return true;
 }
 
@@ -326,7 +327,7 @@ wlb_status wlb_create(const wlb_params *p, void *device_workspace, size_t worksp
     // SMs, and one step per launch is faster there
     if (h->g.dim == 3) {
         cudaError_t pe = cudaSuccess;
-        if (two_step_plan(h, 0, 1, 0, 0, &h->two_plan, &pe) && pe == cudaSuccess) {
+        if (two_step_plan(h, 0, 1, 0, 0, 0, &h->two_plan, &pe) && pe == cudaSuccess) {
             h->two_step = true;
             h->two_mode = 1;
         }
@@ -527,11 +528,11 @@ wlb_status wlb_mask(wlb_handle *h, unsigned char *mask_out) {
 namespace {
 
 // Plan two steps per launch with the handle's settings and switch to it.
-wlb_status replan_two_step(wlb_handle *h, int enable, int slab_rows, int tiles, int staging) {
+wlb_status replan_two_step(wlb_handle *h, int enable, int slab_rows, int tiles, int staging, int c2) {
     wlb::TwoStepPlan plan;
     if (enable) {
         cudaError_t e = cudaSuccess;
-        if (!two_step_plan(h, slab_rows, enable, tiles, staging, &plan, &e))
+        if (!two_step_plan(h, slab_rows, enable, tiles, staging, c2, &plan, &e))
             return fail(h, WLB_ERR_ARG,
                         "two steps per launch need a periodic lattice: 3D FP32/FP16 rows of 16-cell multiples, or 2D "
                         "rows of at most 8 values per lane (no slab height, no x-tiles)");
@@ -540,7 +541,7 @@ wlb_status replan_two_step(wlb_handle *h, int enable, int slab_rows, int tiles, 
     const bool same = (enable != 0) == h->two_step && plan.H == h->two_plan.H && plan.zc == h->two_plan.zc &&
                       plan.nseg == h->two_plan.nseg && plan.chunks_per_lane == h->two_plan.chunks_per_lane &&
                       plan.ntile == h->two_plan.ntile && plan.tx == h->two_plan.tx &&
-                      plan.producer == h->two_plan.producer;
+                      plan.producer == h->two_plan.producer && plan.c2_staged == h->two_plan.c2_staged;
     if (!same) {
         destroy_graphs(h);  // unsampled period graphs change shape
         h->two_step = enable != 0;
@@ -550,6 +551,7 @@ wlb_status replan_two_step(wlb_handle *h, int enable, int slab_rows, int tiles, 
     h->two_rows = slab_rows;
     h->two_tiles = tiles;
     h->two_staging = staging;
+    h->two_c2 = c2;
     return WLB_OK;
 }
 
@@ -558,21 +560,28 @@ wlb_status replan_two_step(wlb_handle *h, int enable, int slab_rows, int tiles, 
 wlb_status wlb_set_two_step(wlb_handle *h, int enable, int slab_rows) {
     if (!h || slab_rows < 0 || enable < 0 || enable > 3) return WLB_ERR_ARG;
     DeviceGuard dg(h->device);
-    return replan_two_step(h, enable, slab_rows, h->two_tiles, h->two_staging);
+    return replan_two_step(h, enable, slab_rows, h->two_tiles, h->two_staging, h->two_c2);
 }
 
 wlb_status wlb_set_two_step_tiles(wlb_handle *h, int tiles) {
     if (!h || tiles < 0) return WLB_ERR_ARG;
     DeviceGuard dg(h->device);
     if (!h->two_mode) return fail(h, WLB_ERR_STATE, "x-tiles apply to two steps per launch, which is off");
-    return replan_two_step(h, h->two_mode, h->two_rows, tiles, h->two_staging);
+    return replan_two_step(h, h->two_mode, h->two_rows, tiles, h->two_staging, h->two_c2);
 }
 
 wlb_status wlb_set_two_step_staging(wlb_handle *h, int staging) {
     if (!h || staging < 0 || staging > 2) return WLB_ERR_ARG;
     DeviceGuard dg(h->device);
     if (!h->two_mode) return fail(h, WLB_ERR_STATE, "the staging warp applies to two steps per launch, which is off");
-    return replan_two_step(h, h->two_mode, h->two_rows, h->two_tiles, staging);
+    return replan_two_step(h, h->two_mode, h->two_rows, h->two_tiles, staging, h->two_c2);
+}
+
+wlb_status wlb_set_two_step_c2(wlb_handle *h, int c2) {
+    if (!h || c2 < 0 || c2 > 2) return WLB_ERR_ARG;
+    DeviceGuard dg(h->device);
+    if (!h->two_mode) return fail(h, WLB_ERR_STATE, "c^2 staging applies to two steps per launch, which is off");
+    return replan_two_step(h, h->two_mode, h->two_rows, h->two_tiles, h->two_staging, c2);
 }
 
 wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out) {
@@ -592,6 +601,7 @@ wlb_status wlb_get_info(const wlb_handle *h, wlb_info *out) {
     out->two_step_segments = h->two_step ? h->two_plan.nseg : 0;
     out->two_step_tiles = h->two_step ? h->two_plan.ntile : 0;
     out->two_step_staging_warp = h->two_step ? h->two_plan.producer : 0;
+    out->two_step_c2_staged = h->two_step && h->g.dim == 3 ? h->two_plan.c2_staged : 0;
     return WLB_OK;
 }
 

@@ -29,7 +29,7 @@ struct wlb_handle {
     bool vector_path = false;
     bool two_step = false;      // unsampled steps two per launch (wlb_set_two_step)
     wlb::TwoStepPlan two_plan;  // its grid, set by wlb_set_two_step
-    int two_mode = 0, two_rows = 0, two_tiles = 0, two_staging = 0;  // the settings it was planned with
+    int two_mode = 0, two_rows = 0, two_tiles = 0, two_staging = 0, two_c2 = 0;  // the settings it was planned with
     wlb::SideStream side;       // sampling beside the two-step update
     double deadline_s = 0.0;    // wlb_run's host-clock limit, 0 = none (wlb_set_deadline)
     cudaEvent_t marks[2] = {nullptr, nullptr};  // period markers of a deadline run

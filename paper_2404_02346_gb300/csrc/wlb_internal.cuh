@@ -90,6 +90,7 @@ struct TwoStepPlan {
     int H = 0, nslab = 0, chunks = 0, zc = 0, nseg = 0, chunks_per_lane = 0, threads = 0;
     int ntile = 1, tx = 0;  // x-tiles per row and their width (1: whole rows)
     int producer = 0;       // whole rows: 1 = a dedicated warp stages the planes
+    int c2_staged = 1;      // whole rows: 1 = band rows' c^2 staged in shared memory, 0 = read from L2
     bool full = false;      // every segment a full warp (no idle lanes)
     size_t smem = 0;
 };
@@ -97,9 +98,11 @@ bool two_step_supported(const Geometry &g, Prec p);
 // slab_rows: 0 picks H; otherwise that H.  mode: 1 automatic, 2 one 16-byte
 // chunk per lane, 3 two.  tiles: 0 automatic, 1 whole rows, n >= 2 n x-tiles
 // per row.  staging: 0 automatic, 1 warp 0 stages planes besides computing,
-// 2 a dedicated staging warp.  Also opts the kernel into the shared memory it
-// needs on the current device.
-cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, int staging,
+// 2 a dedicated staging warp.  c2 (whole rows): 0 stages band rows' c^2 in
+// shared memory where the slab still fits, 1 always, 2 never (S1 reads it
+// from global memory, prefetched into L2).  Also opts the kernel into the
+// shared memory it needs on the current device.
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, int staging, int c2,
                            TwoStepPlan *out);
 // Side stream and events that let the sampling kernel of a sampled two-step
 // launch run beside the update (fork before, join after).

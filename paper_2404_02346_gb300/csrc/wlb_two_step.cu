@@ -61,12 +61,20 @@ constexpr int two_step_threads() {
     return Store<S>::W * CH <= 4 ? 32 * kMaxRows : 32 * 12;
 }
 
-// Shared memory per S1 row: two staged planes of seven populations (storage
-// type), of the class bytes and of c^2 (arithmetic type; copied only for rows
-// holding interface-band cells), and the three-plane ring of the two exchanged
-// populations (storage type).
-constexpr size_t smem_per_row(size_t row_bytes, size_t c2_row_bytes, size_t cls_row_bytes) {
-    return (size_t)kStages * (7 * row_bytes + c2_row_bytes + cls_row_bytes) + (size_t)kRingPlanes * 2 * row_bytes;
+// Dynamic shared memory of a whole-row slab of H rows (H + 2 S1 rows) in
+// nseg segments: two staged planes of the seven populations (storage type),
+// of the class bytes and, with c2_staged, of c^2 (arithmetic type; copied
+// only for rows holding interface-band cells); the three-plane +-y exchange
+// ring, H rows per population (+y of S1 rows 0 .. H-1 and -y of rows
+// 2 .. H+1: the only ones step 2 pulls); the segment-end ring, the stage
+// barriers and the staged rows' band flags.
+template <typename S>
+size_t whole_row_smem(int nx, int nseg, int H, bool c2_staged) {
+    using R = typename Store<S>::R;
+    const size_t rmax = (size_t)H + 2, n = (size_t)nx;
+    return (size_t)kStages * rmax * (7 * n * sizeof(S) + (c2_staged ? n * sizeof(R) : 0) + n) +
+           (size_t)kRingPlanes * 2 * (size_t)H * n * sizeof(S) + (size_t)kRingPlanes * rmax * nseg * 2 * sizeof(R) +
+           (size_t)kStages * sizeof(uint64_t) + (size_t)kStages * rmax;
 }
 
 // Halo cells staged on either side of an x-tile: 16 bytes of each array.
@@ -173,6 +181,26 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(saddr(dst)),
         "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(saddr(bar))
         : "memory");
+}
+
+// Prefetch `bytes` at `src` into L2 (16-byte aligned, a multiple of 16 bytes).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(src)), "r"(bytes)
+                 : "memory");
+}
+
+// W consecutive FP32 values at p (16-byte aligned; shared or global memory).
+template <int W>
+__device__ __forceinline__ void load_row_vec(const float *p, float (&v)[W]) {
+    static_assert(W % 4 == 0, "whole 16-byte vectors");
+#pragma unroll
+    for (int j = 0; j < W / 4; ++j) {
+        const float4 t = *reinterpret_cast<const float4 *>(p + 4 * j);
+        v[4 * j] = t.x;
+        v[4 * j + 1] = t.y;
+        v[4 * j + 2] = t.z;
+        v[4 * j + 3] = t.w;
+    }
 }
 
 // The collision of the one-step kernels (collide_half), pulled populations
@@ -283,12 +311,21 @@ struct SlabParams {
     int H, nslab, zc, nseg;  // plan
     int ntile, tx;           // x-tiles per row and their width in cells (ntile = 1: whole rows)
     int producer;            // whole rows: 1 = warp nseg * (H + 2) only stages planes, 0 = warp 0 also computes
+    int c2_staged;           // whole rows, kernels with C2 = 0: 1 = band rows' c^2 staged in shared memory,
+                             // 0 = read from global memory (prefetched into L2 with the plane's copies)
     int *err;
 };
 
 // The sweep of CTA `cta` of a lattice (slab cta % nslab, z-chunk cta / nslab)
-// in the dynamic shared memory `smem`.  Block-uniform control flow.
-template <typename S, int CH, bool FULL>
+// in the dynamic shared memory `smem`.  Block-uniform control flow.  C2 = 1:
+// band rows' c^2 staged in shared memory (fixed at compile time); C2 = 0:
+// P.c2_staged chooses at run time between that and S1 reading c^2 from
+// global memory, where the staging warp prefetched it into L2 two planes
+// ahead.  The plans that read from L2 launch the C2 = 0 form: at 512^3 FP32
+// (4-row slabs) it took 1174 us per launch against 1202 us for a form
+// compiled for L2 reads only (same registers; the compiler schedules the
+// sweep differently).
+template <typename S, int CH, bool FULL, int C2>
 __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsigned char *smem) {
     // rows of nx = V * W cells, V 16-byte vectors, split into nseg segments
     // of up to 32 * CH vectors (the last one may be shorter; FULL: none is)
@@ -305,11 +342,13 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
     int *err = P.err;
     const int rmax = H + 2;
     const size_t rowel = (size_t)nx;
+    const bool c2_staged = C2 == 1 || P.c2_staged != 0;
+    // the layout of whole_row_smem
     S *stage = reinterpret_cast<S *>(smem);                                          // [kStages][7][rmax][nx]
-    R *c2s = reinterpret_cast<R *>(stage + (size_t)kStages * 7 * rmax * rowel);      // [kStages][rmax][nx]
-    uint8_t *clss = reinterpret_cast<uint8_t *>(c2s + (size_t)kStages * rmax * rowel);  // [kStages][rmax][nx]
-    S *ring = reinterpret_cast<S *>(clss + (size_t)kStages * rmax * rowel);         // [kRingPlanes][2][rmax][nx]
-    R *edge = reinterpret_cast<R *>(ring + (size_t)kRingPlanes * 2 * rmax * rowel);  // [kRingPlanes][rmax][nseg][2]
+    R *c2s = reinterpret_cast<R *>(stage + (size_t)kStages * 7 * rmax * rowel);      // [kStages][rmax][nx] or none
+    uint8_t *clss = reinterpret_cast<uint8_t *>(c2s + (c2_staged ? (size_t)kStages * rmax * rowel : 0));
+    S *ring = reinterpret_cast<S *>(clss + (size_t)kStages * rmax * rowel);         // [kRingPlanes][2][H][nx]
+    R *edge = reinterpret_cast<R *>(ring + (size_t)kRingPlanes * 2 * H * rowel);     // [kRingPlanes][rmax][nseg][2]
     uint64_t *bar = reinterpret_cast<uint64_t *>(edge + (size_t)kRingPlanes * rmax * nseg * 2);  // [kStages]
     uint8_t *rowflag = reinterpret_cast<uint8_t *>(bar + kStages);  // [kStages][rmax]: row holds band cells
 
@@ -341,14 +380,16 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
     // lane i < 8 of the issuing warp copies population i (i = 7: the class bytes) for
     // the rs rows, one bulk copy per run of rows that is contiguous in memory
     // (two where the slab's halo wraps around y); lane 8 + r copies the c^2 row
-    // of S1 row r when that row holds band cells (flag).
+    // of S1 row r when that row holds band cells (flag), or without c^2
+    // staging prefetches it into L2 for S1's own loads two planes later.
     auto issue = [&](int k, int flag) {
         const unsigned band = __ballot_sync(kFull, flag != 0);
         const int p = (za - 1 + k + nz) % nz;
         const int buf = k % kStages;
         if (lane < rs) rowflag[buf * rmax + lane] = flag != 0;  // read by S1 after a barrier
         if (lane == 0)
-            bar_expect(&bar[buf], (uint32_t)rs * (7u * row_bytes + (uint32_t)nx) + (uint32_t)__popc(band) * c2_bytes);
+            bar_expect(&bar[buf], (uint32_t)rs * (7u * row_bytes + (uint32_t)nx) +
+                                      (c2_staged ? (uint32_t)__popc(band) * c2_bytes : 0u));
         __syncwarp();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage
         if (lane < 8) {
@@ -370,7 +411,10 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
         } else if (lane - 8 < rs && ((band >> (lane - 8)) & 1u)) {
             const int r = lane - 8;
             const long long row0 = (long long)p * ny + (y0 - 1 + r + ny) % ny;
-            bulk_load(c2s + ((size_t)buf * rmax + r) * rowel, c2f + row0 * nx, c2_bytes, &bar[buf]);
+            if (c2_staged)
+                bulk_load(c2s + ((size_t)buf * rmax + r) * rowel, c2f + row0 * nx, c2_bytes, &bar[buf]);
+            else
+                bulk_prefetch_l2(c2f + row0 * nx, c2_bytes);
         }
     };
     int flag_next = 0;  // issuing warp: band flag of plane index k + kStages, for the issue in iteration k
@@ -407,7 +451,8 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
         R cs[CH][W];
         if (s1_row) {
             const S *st = stage + ((size_t)buf * 7 * rmax + row) * rowel;
-            const R *cst = c2s + ((size_t)buf * rmax + row) * rowel;
+            // c^2 row of band rows: staged, or in global memory (L2)
+            const R *cst = c2_staged ? c2s + ((size_t)buf * rmax + row) * rowel : c2f + ((long long)p * ny + y) * nx;
             const uint8_t *clt = clss + ((size_t)buf * rmax + row) * rowel;
             const bool band_row = rowflag[buf * rmax + row] != 0;  // warp-uniform
             R f[7][CH][W];
@@ -427,10 +472,17 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
                 // interface-band cells holds only fluid and object cells
                 const unsigned long long cl = act[c] ? load_classes<W>(clt + x0) : 0ull;
                 if (band_row) {
+                    R cv[W];
+                    if constexpr (C2 == 1) {
+#pragma unroll
+                        for (int e = 0; e < W; ++e) cv[e] = act[c] ? cst[x0 + e] : c0sq;
+                    } else {
+                        if (act[c]) load_row_vec<W>(cst + x0, cv);
+                    }
 #pragma unroll
                     for (int e = 0; e < W; ++e) {
                         const unsigned kc = (unsigned)(cl >> (8 * e)) & 0xffu;
-                        cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : (act[c] ? cst[x0 + e] : c0sq));
+                        cs[c][e] = kc == CELL_FLUID ? c0sq : (kc == CELL_OBJECT ? cpsq : (act[c] ? cv[e] : c0sq));
                     }
                 } else {
 #pragma unroll
@@ -446,7 +498,8 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
             }
             R fpx[CH][W], fmx[CH][W];
             shift_x<R, CH, W>(f[1], f[2], lane, vg, whole, left, right, fpx, fmx);
-            S *ry = ring + ((size_t)(k % kRingPlanes) * 2 * rmax + row) * rowel;
+            // ring plane k: +y of rows 0 .. H-1, then -y of rows 2 .. H+1
+            S *ry = ring + (size_t)(k % kRingPlanes) * 2 * H * rowel;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const int x0 = xs + (c * 32 + lane) * W;
@@ -467,8 +520,8 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
                 const R (&oy)[W] = o[3];
                 const R (&omy)[W] = o[4];
                 if (act[c]) {
-                    Vec<S>::st(ry + x0, oy);                        // +y of row w
-                    Vec<S>::st(ry + (size_t)rmax * rowel + x0, omy);  // -y of row w
+                    if (row < hs) Vec<S>::st(ry + (size_t)row * rowel + x0, oy);                // +y, S2 of row + 1
+                    if (row >= 2) Vec<S>::st(ry + (size_t)(H + row - 2) * rowel + x0, omy);  // -y, S2 of row - 1
                 }
             }
             // the segment's end values for the neighbouring segments' S2
@@ -492,7 +545,7 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
         if (k >= 2 && s2_row) {
             const int q = (p + nz - 1) % nz;
             const long long r0 = ((long long)q * ny + y) * nx;
-            const S *ry = ring + (size_t)((k - 1) % kRingPlanes) * 2 * rmax * rowel;
+            const S *ry = ring + (size_t)((k - 1) % kRingPlanes) * 2 * H * rowel;
             R left = R(0), right = R(0);
             if (!whole) {
                 const R *ed = edge + ((size_t)((k - 1) % kRingPlanes) * rmax + row) * nseg * 2;
@@ -506,8 +559,8 @@ __device__ __forceinline__ void slab_body(const SlabParams<S> &P, int cta, unsig
                 if (!act[c]) continue;
                 const int x0 = xs + (c * 32 + lane) * W;
                 R fpy[W], fmy[W];
-                Vec<S>::ld(ry + (size_t)(row - 1) * rowel + x0, fpy);             // +y of row w-1
-                Vec<S>::ld(ry + (size_t)(rmax + row + 1) * rowel + x0, fmy);      // -y of row w+1
+                Vec<S>::ld(ry + (size_t)(row - 1) * rowel + x0, fpy);      // +y of row w-1
+                Vec<S>::ld(ry + (size_t)(H + row - 1) * rowel + x0, fmy);  // -y of row w+1
                 R o[7][W];
 #pragma unroll
                 for (int e = 0; e < W; ++e) {
@@ -810,13 +863,13 @@ __device__ __forceinline__ void slab_body_tiled(const SlabParams<S> &P, int cta,
     cp_async_wait<0>();
 }
 
-template <typename S, int CH, bool FULL, bool TILED>
+template <typename S, int CH, bool FULL, bool TILED, int C2>
 __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1) update2_slab(SlabParams<S> P) {
     extern __shared__ __align__(128) unsigned char smem[];
     if constexpr (TILED)
-        slab_body_tiled<S, CH, FULL>(P, blockIdx.x, smem);
+        slab_body_tiled<S, CH, FULL>(P, blockIdx.x, smem);  // stages c^2 itself
     else
-        slab_body<S, CH, FULL>(P, blockIdx.x, smem);
+        slab_body<S, CH, FULL, C2>(P, blockIdx.x, smem);
 }
 
 // Batched ensembles: CTA j sweeps CTA j - cta_first[i] of lattice
@@ -856,8 +909,9 @@ __global__ void __launch_bounds__(two_step_threads<S, CH>(), 1)
         P.ntile = 1;
         P.tx = P.nx;
         P.producer = L.plan.producer;
+        P.c2_staged = 1;
         P.err = L.b.err;
-        slab_body<S, CH, FULL>(P, j - cta_first[i], smem);
+        slab_body<S, CH, FULL, 1>(P, j - cta_first[i], smem);
     }
     if (!advance) return;
     __syncthreads();
@@ -939,12 +993,23 @@ int chunks_for(int V, int mode) {
 // the last tile possibly narrower; ntile = 1: the whole row).
 inline int tile_width(int nx, int ntile) { return ntile <= 1 ? nx : ((nx + ntile - 1) / ntile + 15) / 16 * 16; }
 
-template <typename S, int CH, bool TILED>
-cudaError_t set_smem_attr(bool full, int smem_max) {
-    return full ? cudaFuncSetAttribute(update2_slab<S, CH, true, TILED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem_max)
-                : cudaFuncSetAttribute(update2_slab<S, CH, false, TILED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem_max);
+// The kernel of a plan: x-tiles or whole rows, full warps or not, and for
+// whole rows c^2 staged (C2 = 1) or read from L2 (C2 = 0, P.c2_staged = 0).
+template <typename S, int CH>
+void (*slab_kernel(const TwoStepPlan &pl))(SlabParams<S>) {
+    if (pl.ntile > 1) return pl.full ? update2_slab<S, CH, true, true, 1> : update2_slab<S, CH, false, true, 1>;
+    if (pl.c2_staged) return pl.full ? update2_slab<S, CH, true, false, 1> : update2_slab<S, CH, false, false, 1>;
+    return pl.full ? update2_slab<S, CH, true, false, 0> : update2_slab<S, CH, false, false, 0>;
+}
+
+// Whether a whole-row slab of H rows fits `smem_max` bytes, and with c^2
+// staged or not: c2 = 0 stages it where it fits, 1 always, 2 never.
+// Returns 1 (staged), 0 (not staged) or -1 (does not fit).
+template <typename S>
+int whole_row_fit(int nx, int nseg, int H, int c2, int smem_max) {
+    if (c2 != 2 && whole_row_smem<S>(nx, nseg, H, true) <= (size_t)smem_max) return 1;
+    if (c2 != 1 && whole_row_smem<S>(nx, nseg, H, false) <= (size_t)smem_max) return 0;
+    return -1;
 }
 
 // Slab height H (rows <= smem and thread limits; `want` > 0 asks for one)
@@ -954,9 +1019,11 @@ cudaError_t set_smem_attr(bool full, int smem_max) {
 // written); FP16 storage, whose planes cost a CTA mostly a fixed latency:
 // waves x planes.  Among heights within 5 % of the best estimate the tallest
 // is taken.  *cost gets the estimate of the chosen plan, *hmax the tallest
-// slab that fits (either may be null).
+// slab that fits (either may be null).  c2: c^2 staging of whole rows
+// (whole_row_fit).
 template <typename S, int CH>
-cudaError_t plan_ch(const Geometry &g, int want, int ntile, int staging, TwoStepPlan *pl, double *cost, int *hmax) {
+cudaError_t plan_ch(const Geometry &g, int want, int ntile, int staging, int c2, TwoStepPlan *pl, double *cost,
+                    int *hmax) {
     using R = typename Store<S>::R;
     constexpr int W = Store<S>::W;
     int dev = 0, sms = 0, smem_max = 0;
@@ -973,14 +1040,13 @@ cudaError_t plan_ch(const Geometry &g, int want, int ntile, int staging, TwoStep
     if (tiled && nseg != 1) return cudaErrorInvalidValue;  // a tile row is one warp
     // whole rows: a dedicated staging warp on request (tiles stage per warp)
     const int producer = !tiled && staging == 2 ? 1 : 0;
-    const size_t per_row_all =
-        tiled ? smem_per_tile_row<S>(tx)
-              : smem_per_row((size_t)nx * sizeof(S), (size_t)nx * sizeof(R), (size_t)nx) +
-                    (size_t)kRingPlanes * nseg * 2 * sizeof(R);
+    const size_t per_tile_row = tiled ? smem_per_tile_row<S>(tx) : 0;
     const size_t fixed = kStages * sizeof(uint64_t) + kStages * (size_t)kMaxRows + 16;
-    int rows = (int)(((size_t)smem_max - fixed) / per_row_all);
-    rows = std::min(rows, (two_step_threads<S, CH>() / 32 - producer) / nseg);
-    rows = std::min(rows, kMaxRows);
+    int rows = std::min((two_step_threads<S, CH>() / 32 - producer) / nseg, kMaxRows);
+    if (tiled)
+        rows = std::min(rows, (int)(((size_t)smem_max - fixed) / per_tile_row));
+    else
+        while (rows >= 3 && whole_row_fit<S>(nx, nseg, rows - 2, c2, smem_max) < 0) --rows;
     if (rows < 3) return cudaErrorInvalidValue;
     if (hmax) *hmax = rows - 2;
     const int h_lo = want > 0 ? want : 1, h_hi = want > 0 ? want : rows - 2;
@@ -1021,12 +1087,18 @@ cudaError_t plan_ch(const Geometry &g, int want, int ntile, int staging, TwoStep
     pl->tx = tx;
     pl->producer = producer;
     pl->threads = 32 * (nseg * (pl->H + 2) + producer);
-    pl->smem = per_row_all * (pl->H + 2) + fixed;
+    if (tiled) {
+        pl->c2_staged = 1;
+        pl->smem = per_tile_row * (pl->H + 2) + fixed;
+    } else {
+        pl->c2_staged = whole_row_fit<S>(nx, nseg, pl->H, c2, smem_max);
+        pl->smem = whole_row_smem<S>(nx, nseg, pl->H, pl->c2_staged != 0);
+    }
     const int last = nx - (tiles - 1) * tx;  // cells of the last tile
     pl->full = (tx / W) % (32 * CH) == 0 && (last / W) % (32 * CH) == 0;
     // the attribute belongs to the kernel, shared by every handle: allow the
     // device's whole opt-in shared memory, not just this plan's
-    return tiled ? set_smem_attr<S, CH, true>(pl->full, smem_max) : set_smem_attr<S, CH, false>(pl->full, smem_max);
+    return cudaFuncSetAttribute(slab_kernel<S, CH>(*pl), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
 }
 
 // Chunks per lane and segments per row for `mode` (1: automatic, 2: one
@@ -1036,18 +1108,35 @@ cudaError_t plan_ch(const Geometry &g, int want, int ntile, int staging, TwoStep
 // take 1254 us per launch against 1410 us for 4 tiles of 14-row slabs);
 // rows too long for that take the cheapest estimate of 2 .. 16 tiles.
 template <typename S>
-cudaError_t plan_for(const Geometry &g, int want, int mode, int tiles, int staging, TwoStepPlan *pl) {
+cudaError_t plan_for(const Geometry &g, int want, int mode, int tiles, int staging, int c2, TwoStepPlan *pl) {
     constexpr int W = Store<S>::W;
     if (!row_vectors<S>(g)) return cudaErrorInvalidValue;
-    auto one = [&](int nt, TwoStepPlan *out, double *cost) -> cudaError_t {
+    auto one_c2 = [&](int nt, int c2v, TwoStepPlan *out, double *cost) -> cudaError_t {
         const int tx = tile_width(g.n[0], nt);
         if (nt > 1 && (g.n[0] + tx - 1) / tx < 2) return cudaErrorInvalidValue;
         // a tile row is one warp: two chunks per lane where one does not cover it
         const int ch = (nt > 1 && mode == 1 && tx / W > 32) ? (Store<S>::W * 2 <= 8 ? 2 : 0) : chunks_for<S>(tx / W, mode);
         if (!ch) return cudaErrorInvalidValue;
-        if (ch == 1) return plan_ch<S, 1>(g, want, nt, staging, out, cost, nullptr);
-        if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, nt, staging, out, cost, nullptr);
+        if (ch == 1) return plan_ch<S, 1>(g, want, nt, staging, c2v, out, cost, nullptr);
+        if constexpr (Store<S>::W * 2 <= 8) return plan_ch<S, 2>(g, want, nt, staging, c2v, out, cost, nullptr);
         return cudaErrorInvalidValue;
+    };
+    // Automatic c^2 staging of whole rows: staged, unless reading it from L2
+    // lets a slab of lower estimated cost fit (512-cell FP32 rows: 4-row slabs
+    // against 3, 1170 against 1238 us per launch).  Where the staged plan is
+    // as cheap, a taller unstaged one is not taken (256^3 FP32: 7-row staged
+    // slabs 150 us, 9-row unstaged 190 us).
+    auto one = [&](int nt, TwoStepPlan *out, double *cost) -> cudaError_t {
+        if (nt > 1 || c2 != 0) return one_c2(nt, c2, out, cost);
+        TwoStepPlan ps, pa;
+        double cs = 0, ca = 0;
+        const cudaError_t es = one_c2(nt, 1, &ps, &cs);
+        const cudaError_t ea = one_c2(nt, 0, &pa, &ca);
+        if (es != cudaSuccess && ea != cudaSuccess) return ea;
+        const bool staged = es == cudaSuccess && (ea != cudaSuccess || cs <= ca);
+        *out = staged ? ps : pa;
+        if (cost) *cost = staged ? cs : ca;
+        return cudaSuccess;
     };
     if (tiles >= 1 && staging != 0) return one(tiles, pl, nullptr);
     if (tiles > 1) return one(tiles, pl, nullptr);
@@ -1109,6 +1198,7 @@ SlabParams<S> slab_params(const Geometry &g, const Buffers &b, const TwoStepPlan
     P.ntile = pl.ntile;
     P.tx = pl.tx;
     P.producer = pl.producer;
+    P.c2_staged = pl.c2_staged;
     P.err = err;
     return P;
 }
@@ -1132,9 +1222,8 @@ cudaError_t launch_ch(const Geometry &g, const Buffers &b, const TwoStepPlan &pl
         if (e == cudaSuccess && fork) e = cudaEventRecord(side.join, side.stream);
         if (e != cudaSuccess) return e;
     }
-    auto kernel = pl.ntile > 1 ? (pl.full ? update2_slab<S, CH, true, true> : update2_slab<S, CH, false, true>)
-                               : (pl.full ? update2_slab<S, CH, true, false> : update2_slab<S, CH, false, false>);
-    kernel<<<pl.ntile * pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(slab_params<S>(g, b, pl, src, err));
+    slab_kernel<S, CH>(pl)<<<pl.ntile * pl.nslab * pl.chunks, pl.threads, pl.smem, s>>>(
+        slab_params<S>(g, b, pl, src, err));
     e = cudaGetLastError();
     if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(s, side.join, 0);  // the next launch overwrites src
     return e;
@@ -1155,18 +1244,18 @@ bool two_step_supported(const Geometry &g, Prec p) {
     if (g.dim != 3 || g.driven) return false;
     TwoStepPlan probe;
     switch (p) {
-        case Prec::F16: return row_vectors<__half>(g) > 0 && plan_for<__half>(g, 0, 1, 0, 0, &probe) == cudaSuccess;
-        case Prec::F32: return row_vectors<float>(g) > 0 && plan_for<float>(g, 0, 1, 0, 0, &probe) == cudaSuccess;
+        case Prec::F16: return row_vectors<__half>(g) > 0 && plan_for<__half>(g, 0, 1, 0, 0, 0, &probe) == cudaSuccess;
+        case Prec::F32: return row_vectors<float>(g) > 0 && plan_for<float>(g, 0, 1, 0, 0, 0, &probe) == cudaSuccess;
         default: return false;
     }
 }
 
-cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, int staging,
+cudaError_t plan_two_steps(const Geometry &g, Prec p, int slab_rows, int mode, int tiles, int staging, int c2,
                            TwoStepPlan *out) {
     TwoStepPlan pl;
     if (g.dim != 3 || g.driven || (p != Prec::F16 && p != Prec::F32)) return cudaErrorInvalidValue;
-    cudaError_t e = p == Prec::F16 ? plan_for<__half>(g, slab_rows, mode, tiles, staging, &pl)
-                                   : plan_for<float>(g, slab_rows, mode, tiles, staging, &pl);
+    cudaError_t e = p == Prec::F16 ? plan_for<__half>(g, slab_rows, mode, tiles, staging, c2, &pl)
+                                   : plan_for<float>(g, slab_rows, mode, tiles, staging, c2, &pl);
     if (e == cudaSuccess) *out = pl;
     return e;
 }
@@ -1190,8 +1279,6 @@ namespace {
 template <typename S, int CH>
 bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, const BatchTwoKnobs &kn,
                 BatchTwoGroup *grp) {
-    using R = typename Store<S>::R;
-    const size_t fixed = kStages * sizeof(uint64_t) + kStages * (size_t)kMaxRows + 16;
     int t_max = 0;
     size_t s_max = 0;
     bool all_full = true;
@@ -1199,14 +1286,11 @@ bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, c
         const Geometry &g = lats[i].g;
         const int V = row_vectors<S>(g);
         const int nseg = (V + 32 * CH - 1) / (32 * CH);
-        const size_t per_row = smem_per_row((size_t)g.n[0] * sizeof(S), (size_t)g.n[0] * sizeof(R), (size_t)g.n[0]) +
-                               (size_t)kRingPlanes * nseg * 2 * sizeof(R);
-        int rows = (int)(((size_t)smem_max - fixed) / per_row);
-        rows = std::min(rows, two_step_threads<S, CH>() / (32 * nseg));
-        if (rows < 3) return false;
         TwoStepPlan pl;
         pl.producer = kn.staging_warp ? 1 : 0;
-        if (pl.producer) rows = std::min(rows, (two_step_threads<S, CH>() / 32 - 1) / nseg);
+        int rows = std::min((two_step_threads<S, CH>() / 32 - pl.producer) / nseg, kMaxRows);
+        // batches stage c^2 (batch_update2 has no other variant)
+        while (rows >= 3 && whole_row_fit<S>(g.n[0], nseg, rows - 2, 1, smem_max) < 0) --rows;
         if (rows < 3) return false;
         pl.H = std::min(rows - 2, g.n[1]);
         if (kn.h_cap > 0) pl.H = std::min(pl.H, kn.h_cap);
@@ -1219,7 +1303,8 @@ bool plan_group(BatchLat *lats, const std::vector<int> &members, int smem_max, c
         pl.nseg = nseg;
         pl.chunks_per_lane = CH;
         pl.threads = 32 * (nseg * (pl.H + 2) + pl.producer);
-        pl.smem = per_row * (pl.H + 2) + fixed;
+        pl.c2_staged = 1;
+        pl.smem = whole_row_smem<S>(g.n[0], nseg, pl.H, true);
         pl.full = V % (32 * CH) == 0;
         lats[i].plan = pl;
         t_max = std::max(t_max, pl.threads);

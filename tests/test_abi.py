@@ -110,6 +110,7 @@ def test_null_arguments(wlb):
     assert L.wlb_set_two_step(None, 1, 0) == wlb.WLB_ERR_ARG
     assert L.wlb_set_two_step_tiles(None, 0) == wlb.WLB_ERR_ARG
     assert L.wlb_set_two_step_staging(None, 0) == wlb.WLB_ERR_ARG
+    assert L.wlb_set_two_step_c2(None, 0) == wlb.WLB_ERR_ARG
     assert L.wlb_average_noalloc(None, 1, None) == wlb.WLB_ERR_ARG
     assert L.wlb_last_error(None) == b""
 

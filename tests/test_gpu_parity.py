@@ -453,6 +453,37 @@ def test_two_step_staging_warp_is_bit_identical(wlb, shape, lam, precision, rows
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("c2", [1, 2])
+@pytest.mark.parametrize("shape,lam,precision,rows", [
+    ((256, 24, 32), 16.0, "f32", (0, 3, 8)),   # one warp per row; ragged last slab for 8
+    ((512, 24, 32), 16.0, "f32", (0, 2, 4)),   # two warps per row
+    ((160, 21, 32), 16.0, "f32", (0, 4)),      # ragged: 40 of 64 vector slots, ragged slabs
+    ((256, 40, 32), 16.0, "f16", (0, 5)),      # FP16 storage (FP32 c^2)
+    ((512, 24, 32), 16.0, "f16", (0, 3)),      # FP16, two warps per row
+])
+def test_two_step_c2_from_l2_is_bit_identical(wlb, shape, lam, precision, rows, c2):
+    """c^2 of interface-band rows staged in shared memory (1) or read by the
+    first step from global memory after an L2 prefetch (2): forces and fields
+    equal one step per launch bit for bit (the objects cross many slabs, so
+    band rows sit in both halo and inner slab rows)."""
+    prob = workloads.problem(3, shape, 2, lam, 3.0, (shape[0] / 2 + 0.25, shape[1] / 2 - 0.5, lam / 8),
+                             cp=0.42, n_surface=200, n_periods=6, n_avg_periods=2)
+    out = []
+    for enable, r in [(0, 0)] + [(1, r) for r in rows]:
+        with wlb.Solver(prob, precision=precision) as s:
+            s.set_two_step(bool(enable), r)
+            if enable:
+                s.set_two_step_c2(c2)
+                info = s.info()
+                assert info.steps_per_launch == 2 and info.two_step_c2_staged == (1 if c2 == 1 else 0)
+            F = s.run()
+            s.step(3)
+            out.append((F,) + s.fields())
+    for o in out[1:]:
+        for a, b in zip(out[0], o):
+            assert np.array_equal(a, b)
+
+
 def test_two_step_x_tiles_for_rows_too_long_for_whole_slabs(wlb):
     """Whole rows wherever a whole-row slab fits (they are faster); 2048-cell
     FP32 rows do not fit, so the automatic plan splits them into tiles of at
