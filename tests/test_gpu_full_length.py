@@ -57,7 +57,7 @@ def _problem(name):
     return mk.problem(name)
 
 
-NAMES = ("sphere256",)
+NAMES = ("sphere256", "sphere512_kz_pi4")
 
 
 def test_goldens_are_the_workload_problems():
