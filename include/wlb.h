@@ -372,7 +372,9 @@ wlb_status wlb_batch_get_info(const wlb_batch *b, wlb_batch_info *out);
 /* Steps two per launch for the whole batch: on by default when all run
  * lengths, windows and periods are even and every lattice is periodic and
  * either 3D with FP32/FP16 rows the two-step slab kernel takes (then one
- * launch of it covers every lattice, each with its own slab plan) or 2D with
+ * launch of it per lane layout covers every lattice, each with its own slab
+ * plan; with two lane layouts the two launches run side by side, the second
+ * on a stream the batch creates and joins back into its own) or 2D with
  * rows of at most 64 sixteen-byte vectors and 8 values per lane (then each
  * warp sweeps a chunk of 32 rows of one lattice, both steps in registers).
  * A batched sampling launch adds the sums of both steps.  Bit-identical to

@@ -252,7 +252,15 @@ cudaError_t launch_batch_update(int ch, const LatHot *lats, const int *row_lat, 
     return cudaGetLastError();
 }
 
+__global__ void batch_advance_step(long long *step) { *step += 2; }
+
 }  // namespace
+
+cudaError_t launch_batch_advance(long long *step, cudaStream_t s) {
+    batch_advance_step<<<1, 1, 0, s>>>(step);
+    return cudaGetLastError();
+}
+
 }  // namespace wlb
 
 using wlb::BatchLat;
@@ -279,6 +287,7 @@ struct wlb_batch {
     long long class_total_rows[wlb::kMaxChunks] = {0};
     long long total_rows = 0, total_points = 0, max_steps = 0, lattice_updates = 0;
     cudaStream_t stream = nullptr, capture = nullptr;
+    wlb::SideStream side;     // 3D two-step groups run side by side on stream (or capture) and side.stream
     void *owned = nullptr;
     double *host_out = nullptr;  // count * 5 doubles (force[4] + flag)
     int threads = 256, blocks_per_sm = 4;
@@ -374,7 +383,7 @@ cudaError_t issue_steps(wlb_batch *b, int nsteps, int threads, int bps, cudaStre
                 b->dim == 3
                     ? wlb::launch_batch_two_steps(b->prec, b->groups, b->ngroups, b->d_lats, b->d_cta_lat,
                                                   b->d_cta_first, b->d_pt_lat, b->d_pt_begin, b->total_points,
-                                                  b->d_step, b->d_done, grid, s)
+                                                  b->d_step, b->d_done, grid, s, b->side)
                     : wlb::launch_batch2d_two_steps(b->prec, b->two_ch, b->two_nx, b->d_lats, b->d_cta_lat, b->d_cta_first,
                                                     b->total_ctas, b->d_pt_lat, b->d_pt_begin, b->total_points,
                                                     b->d_step, b->d_done, grid, s);
@@ -675,6 +684,9 @@ wlb_status wlb_batch_create(const wlb_params *ps, int count, void *ws, size_t ws
     if (e == cudaSuccess) e = cudaMemcpy(b->d_row_begin, rows.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_pt_begin, pts.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->host_out, sizeof(double) * 5 * count, cudaHostAllocDefault);
     if (e != cudaSuccess) {
         wlb_batch_destroy(b);
@@ -878,6 +890,9 @@ wlb_status wlb_batch_destroy(wlb_batch *b) {
     if (!b) return WLB_ERR_ARG;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->side.stream) cudaStreamDestroy(b->side.stream);
+    if (b->side.fork) cudaEventDestroy(b->side.fork);
+    if (b->side.join) cudaEventDestroy(b->side.join);
     if (b->host_out) cudaFreeHost(b->host_out);
     if (b->owned) cudaFree(b->owned);
     delete b;

@@ -151,11 +151,17 @@ bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, const BatchTwoKnobs
 // One launch of two steps for every active lattice: CTA j of the table works
 // on lattice cta_lat[j] (its CTA j - cta_first[lattice]); with points, a
 // sampling launch before it adds the sums of both steps.  The state at step t
-// is in buffer (t / 2) & 1; the last group's launch advances *step by 2.
+// is in buffer (t / 2) & 1; the last CTA of all groups to finish advances
+// *step by 2.  With two groups and side.stream set, the second group runs on
+// side.stream beside the first (forked after the sampling launch, joined back
+// into s), so each group's partly filled last wave overlaps the other group.
 cudaError_t launch_batch_two_steps(Prec p, const BatchTwoGroup *groups, int ngroups, const BatchLat *lats,
                                    const int *cta_lat, const int *cta_first, const int *pt_lat,
                                    const long long *pt_begin, long long total_points, long long *step,
-                                   unsigned *done, int sample_grid, cudaStream_t s);
+                                   unsigned *done, int sample_grid, cudaStream_t s, const SideStream &side);
+// *step += 2 by one thread on s (wlb_batch.cu): the batched step's advance
+// when its groups ran side by side.
+cudaError_t launch_batch_advance(long long *step, cudaStream_t s);
 
 // Two steps per launch for a single 2D lattice (wlb_two_step_2d.cu): periodic,
 // rows of at most two 16-byte chunks (8 values) per lane; each warp sweeps a

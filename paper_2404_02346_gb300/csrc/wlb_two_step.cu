@@ -1352,32 +1352,47 @@ bool plan_batch_for(BatchLat *lats, int count, const BatchTwoKnobs &kn, BatchTwo
     return true;
 }
 
+// The groups' launches after the sampling launch: one after the other on s,
+// the last one advancing the step; or, with a side stream and two groups,
+// side by side (the second on the side stream, forked and joined by events),
+// neither advancing it, and then a one-thread launch on s advances it once
+// every CTA of both has read it.
 template <typename S>
 cudaError_t launch_batch_for(const BatchTwoGroup *groups, int ngroups, const BatchLat *lats, const int *cta_lat,
                              const int *cta_first, const int *pt_lat, const long long *pt_begin,
                              long long total_points, long long *step, unsigned *done, int sample_grid,
-                             cudaStream_t s) {
+                             cudaStream_t s, const SideStream &side) {
+    cudaError_t e = cudaSuccess;
     if (total_points > 0) {
         batch_sample_two<S><<<sample_grid, 256, 0, s>>>(lats, pt_lat, pt_begin, total_points, step);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const bool fork = ngroups > 1 && side.stream;
+    if (fork) {
+        if ((e = cudaEventRecord(side.fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side.stream, side.fork, 0)) != cudaSuccess) return e;
     }
     for (int k = 0; k < ngroups; ++k) {
         const BatchTwoGroup &G = groups[k];
-        const int adv = k == ngroups - 1;
+        const int adv = !fork && k == ngroups - 1;
+        cudaStream_t sk = fork && k > 0 ? side.stream : s;
         if (G.ch == 1) {
             auto kernel = G.full ? batch_update2<S, 1, true> : batch_update2<S, 1, false>;
-            kernel<<<G.ctas, G.threads, G.smem, s>>>(lats, cta_lat, cta_first, G.cta_begin, adv, step, done);
+            kernel<<<G.ctas, G.threads, G.smem, sk>>>(lats, cta_lat, cta_first, G.cta_begin, adv, step, done);
         } else if constexpr (Store<S>::W * 2 <= 8) {
             auto kernel = G.full ? batch_update2<S, 2, true> : batch_update2<S, 2, false>;
-            kernel<<<G.ctas, G.threads, G.smem, s>>>(lats, cta_lat, cta_first, G.cta_begin, adv, step, done);
+            kernel<<<G.ctas, G.threads, G.smem, sk>>>(lats, cta_lat, cta_first, G.cta_begin, adv, step, done);
         } else {
             return cudaErrorInvalidValue;
         }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    if (fork) {
+        if ((e = cudaEventRecord(side.join, side.stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, side.join, 0)) != cudaSuccess) return e;
+        e = launch_batch_advance(step, s);
+    }
+    return e;
 }
 
 }  // namespace
@@ -1394,14 +1409,14 @@ bool plan_batch_two_steps(Prec p, BatchLat *lats, int count, const BatchTwoKnobs
 cudaError_t launch_batch_two_steps(Prec p, const BatchTwoGroup *groups, int ngroups, const BatchLat *lats,
                                    const int *cta_lat, const int *cta_first, const int *pt_lat,
                                    const long long *pt_begin, long long total_points, long long *step,
-                                   unsigned *done, int sample_grid, cudaStream_t s) {
+                                   unsigned *done, int sample_grid, cudaStream_t s, const SideStream &side) {
     switch (p) {
         case Prec::F16:
             return launch_batch_for<__half>(groups, ngroups, lats, cta_lat, cta_first, pt_lat, pt_begin,
-                                            total_points, step, done, sample_grid, s);
+                                            total_points, step, done, sample_grid, s, side);
         case Prec::F32:
             return launch_batch_for<float>(groups, ngroups, lats, cta_lat, cta_first, pt_lat, pt_begin,
-                                           total_points, step, done, sample_grid, s);
+                                           total_points, step, done, sample_grid, s, side);
         default: return cudaErrorInvalidValue;
     }
 }
