@@ -130,6 +130,8 @@ def test_sphere_512_full_size_short_run(wlb, precision, force_rtol):
         assert info.steps_per_launch == 2
         if precision == "f32":  # whole rows: two warps of two chunks per row
             assert info.two_step_tiles == 1 and info.two_step_segments == 2
+            # 4-row slabs fit 227 KB of shared memory only with c^2 read from L2
+            assert info.two_step_rows == 4 and info.two_step_c2_staged == 0
         s.init()
         s.step(4, sample=False)
         s.step(4, sample=True)
@@ -494,6 +496,8 @@ def test_two_step_x_tiles_for_rows_too_long_for_whole_slabs(wlb):
                                  n_periods=2, n_avg_periods=1)
         with wlb.Solver(prob, precision=precision) as s:
             assert s.info().two_step_tiles == 1, (nx, precision)
+            # c^2 staged wherever that costs no slab height (256-cell rows, FP16)
+            assert s.info().two_step_c2_staged == (0 if (nx, precision) == (512, "f32") else 1), (nx, precision)
     wide = workloads.problem(3, (2048, 24, 32), 2, 16.0, 3.0, (1024.25, 11.5, 2.0), cp=0.42, n_surface=200,
                              n_periods=4, n_avg_periods=2)
     with wlb.Solver(wide) as s:
