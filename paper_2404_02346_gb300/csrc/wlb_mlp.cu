@@ -99,9 +99,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Inputs are mapped to [-1, 1] by the training box before the BF16 rounding.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// tcgen05.ld of 32 columns without the wait, and the wait that completes it:
+// the wait names the destination registers, so no read of them moves above it.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -111,11 +111,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
+// Inputs are mapped to [-1, 1] by the training box before the BF16 rounding.
 __device__ __forceinline__ float normalise_input(float x, float lo, float hi) {
     return 2.0f * (x - lo) / (hi - lo) - 1.0f;
 }
@@ -159,11 +167,6 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
 __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
     unsigned long long d;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 __device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
@@ -549,15 +552,22 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_forward_fused(Fused a) {
                 if (layer < 3) {
                     // bias + GELU -> BF16 -> the next layer's A operand
                     const float *bias = s_bias[layer];
+                    // each column block's TMEM load is issued before the previous block's
+                    // arithmetic, so its latency overlaps it
+                    uint32_t rbuf[2][32];
+                    tmem_ld32_issue(trow + (uint32_t)col0, rbuf[0]);
+                    tmem_ld_wait(rbuf[0]);
+#pragma unroll
                     for (int cb = 0; cb < kHid / 2 / 32; ++cb) {
                         const int n0 = col0 + 32 * cb;
-                        float v[32];
-                        tmem_ld32(trow + (uint32_t)n0, v);
+                        if (cb + 1 < kHid / 2 / 32) tmem_ld32_issue(trow + (uint32_t)(n0 + 32), rbuf[(cb + 1) & 1]);
+                        const uint32_t (&r)[32] = rbuf[cb & 1];
                         uint32_t pk[16];
 #pragma unroll
                         for (int e = 0; e < 32; e += 2) {
                             float g0, g1;
-                            gelu2(__fadd_rn(v[e], bias[n0 + e]), __fadd_rn(v[e + 1], bias[n0 + e + 1]), g0, g1);
+                            gelu2(__fadd_rn(__uint_as_float(r[e]), bias[n0 + e]),
+                                  __fadd_rn(__uint_as_float(r[e + 1]), bias[n0 + e + 1]), g0, g1);
                             const __nv_bfloat162 h = __floats2bfloat162_rn(g0, g1);
                             pk[e / 2] = *reinterpret_cast<const uint32_t *>(&h);
                         }
@@ -566,6 +576,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_forward_fused(Fused a) {
                         for (int g = 0; g < 4; ++g)
                             *reinterpret_cast<uint4 *>(dst + 128 * g) =
                                 make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                        if (cb + 1 < kHid / 2 / 32) tmem_ld_wait(rbuf[(cb + 1) & 1]);
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
