@@ -512,8 +512,8 @@ wlb_status wlb_set_two_step_staging(wlb_handle *h, int staging);
  * takes slab height from long rows (512-cell FP32 rows: 3-row slabs with it,
  * 4 without); otherwise the first step reads it from global memory, where
  * the staging warp has prefetched the row into L2 two planes ahead.  c2: 0
- * lets the library choose (staged wherever the slab height allows it), 1
- * staged, 2 read from L2.  Bit-identical either way.  Applies to the current
+ * lets the library choose (staged, unless reading from L2 fits a slab plan
+ * of lower estimated time than every staged one), 1 staged, 2 read from L2.  Bit-identical either way.  Applies to the current
  * and later wlb_set_two_step settings; x-tiles always stage it.
  * WLB_ERR_STATE while two steps per launch is off; WLB_ERR_ARG if the plan
  * does not fit (setting unchanged) or on a 2D lattice (c2 != 0).  The paper
