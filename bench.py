@@ -96,14 +96,15 @@ def _traffic(kernel_src_sha, steps_per_launch=1, edge=256, name=None):
 HOST_MARKER = b"// ---------------------------------------------------------------- host side: plans and launches"
 
 
-def _kernel_sha(steps_per_launch=1):
+def _kernel_sha(steps_per_launch=1, two_step_src="wlb_two_step.cu"):
     """sha256 over the update kernel's device code and the device header it
-    includes: wlb_step.cu whole, or wlb_two_step.cu up to its host-side part
-    (plans and launches, which a profile's counters do not depend on)."""
+    includes: wlb_step.cu whole, or the two-step source (wlb_two_step.cu, or
+    wlb_two_step_2d.cu for the 2D batches) up to its host-side part (plans and
+    launches, which a profile's counters do not depend on)."""
     csrc = os.path.join(ROOT, "paper_2404_02346_gb300", "csrc")
     h = hashlib.sha256()
     if steps_per_launch == 2:
-        text = open(os.path.join(csrc, "wlb_two_step.cu"), "rb").read()
+        text = open(os.path.join(csrc, two_step_src), "rb").read()
         cut = text.find(HOST_MARKER)
         h.update(text if cut < 0 else text[:cut])
     else:
@@ -510,11 +511,13 @@ def run_ensemble(args):
         lu_per_force = info.lattice_updates / len(probs)
         cpu = dict(cpu, glups=cpu["value"], value=cpu["value"] * 1e9 / lu_per_force, unit="forces/s",
                    sample=cpu["sample"] + "; forces/s at the ensemble's mean %.3g LU per force" % lu_per_force)
-    # DRAM bytes of one two-step pass from the committed ncu summary (the
-    # 64-lattice FP32 ensemble only)
+    # DRAM bytes of one two-step pass from the committed ncu summaries (the
+    # 64-lattice 3D and 512-lattice 2D FP32 ensembles only)
     traffic = None
     if args.workload == "ensemble3d" and args.precision == "f32" and len(probs) == 64 and spl == 2:
         traffic = _traffic(_kernel_sha(2), name="batch_update2_d3q7_f32_ensemble64.md")
+    elif args.workload == "ensemble2d" and args.precision == "f32" and len(probs) == 512 and spl == 2:
+        traffic = _traffic(_kernel_sha(2, "wlb_two_step_2d.cu"), name="batch2d_update2_d2q5_f32_ensemble512.md")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": ("batched two-step update" if spl == 2 else "batched update")
                                           + " (%s storage), all lattices" % args.precision,

@@ -22,7 +22,8 @@
 namespace wlb {
 namespace {
 
-constexpr int kRowsPerWarp = 32;   // row chunk of one warp (two halo rows per chunk)
+constexpr int kRowsPerWarp = 32;   // row chunk of one warp (two halo rows per chunk), at most
+constexpr int kMinRowsPerWarp = 8;  // batches: shortest chunk the planner considers
 constexpr int kWarpsPerBlock = 2;  // small blocks: as many warps per SM as registers allow
 constexpr int kDepth = 3;          // rows staged ahead per warp (shared memory)
 
@@ -402,6 +403,8 @@ __global__ void __launch_bounds__(256) sample_two_2d(Geometry g, const int4 *__r
     });
 }
 
+// ---------------------------------------------------------------- host side: plans and launches
+
 // Chunks per lane for a 2D row of nx cells: 0 if it is not a whole number of
 // 16-byte vectors or needs more than two chunks / eight values per lane.
 template <typename S>
@@ -445,13 +448,49 @@ bool plan_for(BatchLat *lats, int count, int *tasks, int *chunks_per_lane, int *
         if (c > 2 || W * c > 8) return false;  // at most 8 values per lane
         ch = c > ch ? c : ch;
         wide = g.n[0] > wide ? g.n[0] : wide;
+    }
+    // Rows per warp chunk, the same for every lattice: the chunks should fill
+    // whole waves of the warps an SM holds (time ~ waves x (rows + 2), the two
+    // halo rows recomputed per chunk).  512 lattices of 192 rows: 32-row chunks
+    // are 3072 warps in 1.68 waves of 1824, 28-row chunks 3584 in 1.96.
+    int slots = 0;
+    {
+        int dev = 0, sms = 0, bps = 0;
+        const size_t smem = (size_t)kWarpsPerBlock * kDepth * 5 * wide * sizeof(S);
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            (ch == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch2d_update2<S, 1>, 32 * kWarpsPerBlock,
+                                                                     smem)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch2d_update2<S, 2>, 32 * kWarpsPerBlock,
+                                                                     smem)) == cudaSuccess)
+            slots = sms * bps * kWarpsPerBlock;
+        cudaGetLastError();
+    }
+    int rows = kRowsPerWarp;
+    if (slots > 0) {
+        long long best = -1;
+        for (int zc = kRowsPerWarp; zc >= kMinRowsPerWarp; --zc) {
+            long long n = 0;
+            for (int i = 0; i < count; ++i) {
+                const int z = lats[i].g.n[1] < zc ? lats[i].g.n[1] : zc;
+                n += (lats[i].g.n[1] + z - 1) / z;
+            }
+            const long long cost = (n + slots - 1) / slots * (zc + 2);
+            if (best < 0 || cost < best) {
+                best = cost;
+                rows = zc;
+            }
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        const Geometry &g = lats[i].g;
         TwoStepPlan pl;
-        pl.zc = g.n[1] < kRowsPerWarp ? g.n[1] : kRowsPerWarp;
+        pl.zc = g.n[1] < rows ? g.n[1] : rows;
         pl.chunks = (g.n[1] + pl.zc - 1) / pl.zc;
         pl.nslab = 1;
         pl.nseg = 1;
         pl.H = 1;
-        pl.chunks_per_lane = c;
+        pl.chunks_per_lane = (g.n[0] / W + 31) / 32;
         pl.threads = 32 * kWarpsPerBlock;
         lats[i].plan = pl;
         total += pl.chunks;

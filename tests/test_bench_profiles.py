@@ -28,6 +28,12 @@ def test_committed_ensemble_profile_matches_current_kernel():
     assert 0.95 * 7.9287e9 < traffic < 1.1 * 7.9287e9  # 57 B x 139.1 M cells per two-step pass
 
 
+def test_committed_ensemble2d_profile_matches_current_kernel():
+    traffic = bench._traffic(bench._kernel_sha(2, "wlb_two_step_2d.cu"), name="batch2d_update2_d2q5_f32_ensemble512.md")
+    assert traffic is not None, "kernel source changed since its profile was captured"
+    assert 0.9 * 7.738e8 < traffic < 1.1 * 7.738e8  # 41 B x 512 x 192^2 cells per two-step launch
+
+
 def test_foreign_source_hash_gives_no_traffic():
     assert bench._traffic("0" * 64, 2) is None
     assert bench._traffic("0" * 64, 1) is None
