@@ -322,8 +322,9 @@ wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, double force_ou
  *                              steps_per_trial steps each (after a fresh setup)
  *                              and keeps the fastest, returned in *best (may be
  *                              NULL).  Two steps per launch (3D): every plan of
- *                              z-chunk length {16, 32, 64, whole} x slab-height
- *                              cap {tallest, 8, 5} x lane layout {one or two
+ *                              z-chunk length {16, 24, 32, 48, 64, 96, whole}
+ *                              x slab-height cap {tallest, 8, 5} x lane
+ *                              layout {one or two
  *                              16-byte chunks per lane for wide rows, one for
  *                              all} x staging {warp 0, a dedicated warp per
  *                              CTA}; 2D two steps: the one plan, timed; one

@@ -725,7 +725,7 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
         if (b->dim == 3) {
             // 3D: every plan of z-chunk length x slab-height cap x lane layout
             // that fits, on the actual batch
-            const int zcs[] = {16, 32, 64, 1 << 20};
+            const int zcs[] = {16, 24, 32, 48, 64, 96, 1 << 20};
             const int caps[] = {0, 8, 5};
             for (int sw = 0; sw < 2 && e == cudaSuccess; ++sw)
             for (int oc = 0; oc < 2 && e == cudaSuccess; ++oc)
