@@ -327,7 +327,8 @@ wlb_status wlb_average_noalloc(wlb_handle *h, long long n_steps, double force_ou
  *                              layout {one or two
  *                              16-byte chunks per lane for wide rows, one for
  *                              all} x staging {warp 0, a dedicated warp per
- *                              CTA}; 2D two steps: the one plan, timed; one
+ *                              CTA}; 2D two steps: rows per warp chunk {the
+ *                              height filling whole waves, 32, 24, 20, 16}; one
  *                              step per launch: threads per block {128, 256} x
  *                              blocks per SM {2, 4, 8, 16}.  Leaves the
  *                              lattices in an advanced state; wlb_batch_run
@@ -344,7 +345,8 @@ typedef struct wlb_batch wlb_batch;
 typedef struct {
     int threads_per_block, blocks_per_sm;
     float ms_per_step;
-    int z_chunk;             /* two steps per launch (3D): z-chunk length target */
+    int z_chunk;             /* two steps per launch: z-chunk length target (3D),
+                                rows per warp chunk (2D)                       */
     int slab_rows_cap;       /* ... slab-height cap (0: the tallest that fits)  */
     int one_chunk_per_lane;  /* ... 1: one 16-byte chunk per lane everywhere   */
     int plans_tried;         /* launch shapes or plans timed                    */

@@ -477,8 +477,8 @@ cudaError_t plan_two(wlb_batch *b, const wlb::BatchTwoKnobs &kn, bool upload_lat
     wlb::BatchTwoGroup groups[2];
     int ngroups = 0, tasks2d = 0, two_ch = b->two_ch, two_nx = b->two_nx;
     const bool planned = b->dim == 3 ? wlb::plan_batch_two_steps(b->prec, lat.data(), count, kn, groups, &ngroups)
-                                     : wlb::plan_batch2d_two_steps(b->prec, lat.data(), count, &tasks2d, &two_ch,
-                                                                   &two_nx);
+                                     : wlb::plan_batch2d_two_steps(b->prec, lat.data(), count, kn.rows_2d, &tasks2d,
+                                                                   &two_ch, &two_nx);
     if (!planned) return cudaErrorInvalidValue;
     // CTA (3D) or warp (2D) -> lattice table, the lattices of each 3D
     // lane-layout group together; first[i] = lattice i's first entry
@@ -750,10 +750,24 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
                     }
             if (e == cudaSuccess && (e = plan_two(b, best_kn, true)) != cudaSuccess) cudaGetLastError();
         } else {
-            float ms = 0;  // 2D: one plan, timed
-            e = trial(&ms);
-            best_ms = ms;
-            tried = 1;
+            // 2D: chunk heights around the wave-filling one
+            const int rows[] = {0, 32, 24, 20, 16};
+            for (int r : rows) {
+                wlb::BatchTwoKnobs kn = b->knobs;
+                kn.rows_2d = r;
+                if (plan_two(b, kn, true) != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                float ms = 0;
+                if ((e = trial(&ms)) != cudaSuccess) break;
+                ++tried;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_kn = kn;
+                }
+            }
+            if (e == cudaSuccess && (e = plan_two(b, best_kn, true)) != cudaSuccess) cudaGetLastError();
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -763,7 +777,7 @@ wlb_status wlb_batch_autotune(wlb_batch *b, int steps_per_trial, wlb_batch_tunin
             best->threads_per_block = b->two_threads;
             best->blocks_per_sm = 1;
             best->ms_per_step = best_ms / steps;
-            best->z_chunk = b->dim == 3 ? best_kn.zc_target : 0;
+            best->z_chunk = b->dim == 3 ? best_kn.zc_target : b->lat[0].plan.zc;
             best->slab_rows_cap = b->dim == 3 ? best_kn.h_cap : 0;
             best->one_chunk_per_lane = b->dim == 3 ? best_kn.one_chunk : 0;
             best->staging_warp = b->dim == 3 ? best_kn.staging_warp : 0;

@@ -142,6 +142,7 @@ struct BatchTwoGroup {
 // staging_warp: a dedicated warp per CTA stages the planes.
 struct BatchTwoKnobs {
     int zc_target = 32, h_cap = 0, one_chunk = 0, staging_warp = 0;
+    int rows_2d = 0;  // 2D: rows per warp chunk (0: chosen to fill whole waves)
 };
 // Plans every lattice (its plan lands in lats[i].plan) and fills up to two
 // groups (cta_begin / ctas are left to the caller); false if some lattice
@@ -174,9 +175,11 @@ cudaError_t launch_two_steps_2d(const Geometry &g, const Buffers &b, Prec p, con
 
 // The same for batches of 2D lattices (wlb_two_step_2d.cu): a warp sweeps a
 // chunk of rows of one lattice.  Plans every lattice (plan.zc rows per chunk,
-// plan.chunks chunks), returns the number of warps, the chunks per lane and
-// the length of the widest row; false if some lattice cannot take it.
-bool plan_batch2d_two_steps(Prec p, BatchLat *lats, int count, int *tasks, int *chunks_per_lane, int *nx_max);
+// plan.chunks chunks; rows > 0 fixes plan.zc, else it is chosen to fill whole
+// waves), returns the number of warps, the chunks per lane and the length of
+// the widest row; false if some lattice cannot take it.
+bool plan_batch2d_two_steps(Prec p, BatchLat *lats, int count, int rows, int *tasks, int *chunks_per_lane,
+                            int *nx_max);
 cudaError_t launch_batch2d_two_steps(Prec p, int chunks_per_lane, int nx_max, const BatchLat *lats, const int *task_lat,
                                      const int *task_first, int total_tasks, const int *pt_lat,
                                      const long long *pt_begin, long long total_points, long long *step,

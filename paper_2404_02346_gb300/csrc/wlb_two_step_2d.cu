@@ -437,7 +437,7 @@ cudaError_t launch_single(const Geometry &g, const Buffers &b, const TwoStepPlan
 }
 
 template <typename S>
-bool plan_for(BatchLat *lats, int count, int *tasks, int *chunks_per_lane, int *nx_max) {
+bool plan_for(BatchLat *lats, int count, int rows_fixed, int *tasks, int *chunks_per_lane, int *nx_max) {
     constexpr int W = Store<S>::W;
     int ch = 1, total = 0, wide = 0;
     for (int i = 0; i < count; ++i) {
@@ -466,8 +466,8 @@ bool plan_for(BatchLat *lats, int count, int *tasks, int *chunks_per_lane, int *
             slots = sms * bps * kWarpsPerBlock;
         cudaGetLastError();
     }
-    int rows = kRowsPerWarp;
-    if (slots > 0) {
+    int rows = rows_fixed > 0 ? rows_fixed : kRowsPerWarp;
+    if (slots > 0 && rows_fixed <= 0) {
         long long best = -1;
         for (int zc = kRowsPerWarp; zc >= kMinRowsPerWarp; --zc) {
             long long n = 0;
@@ -528,11 +528,12 @@ cudaError_t launch_for(int ch, int nx_max, const BatchLat *lats, const int *task
 
 }  // namespace
 
-bool plan_batch2d_two_steps(Prec p, BatchLat *lats, int count, int *tasks, int *chunks_per_lane, int *nx_max) {
+bool plan_batch2d_two_steps(Prec p, BatchLat *lats, int count, int rows, int *tasks, int *chunks_per_lane,
+                            int *nx_max) {
     switch (p) {
-        case Prec::F16: return plan_for<__half>(lats, count, tasks, chunks_per_lane, nx_max);
-        case Prec::F64: return plan_for<double>(lats, count, tasks, chunks_per_lane, nx_max);
-        default: return plan_for<float>(lats, count, tasks, chunks_per_lane, nx_max);
+        case Prec::F16: return plan_for<__half>(lats, count, rows, tasks, chunks_per_lane, nx_max);
+        case Prec::F64: return plan_for<double>(lats, count, rows, tasks, chunks_per_lane, nx_max);
+        default: return plan_for<float>(lats, count, rows, tasks, chunks_per_lane, nx_max);
     }
 }
 
