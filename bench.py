@@ -64,10 +64,10 @@ def _peaks():
         return None
 
 
-def _profile_name(steps_per_launch=1, edge=256):
-    """Committed ncu summary of the FP32 update kernel on an edge^3 lattice."""
+def _profile_name(steps_per_launch=1, edge=256, precision="f32"):
+    """Committed ncu summary of the update kernel on an edge^3 lattice."""
     kernel = "update2_slab" if steps_per_launch == 2 else "update_rows"
-    return "%s_d3q7_f32_%dcubed.md" % (kernel, edge)
+    return "%s_d3q7_%s_%dcubed.md" % (kernel, precision, edge)
 
 
 def _traffic(kernel_src_sha, steps_per_launch=1, edge=256, name=None):
@@ -381,7 +381,8 @@ def run_gpu(args, probs):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    traffic = _traffic(_kernel_sha(spl), spl, edge) if args.precision == "f32" else None
+    traffic = (_traffic(_kernel_sha(spl), spl, edge, name=_profile_name(spl, edge, args.precision))
+               if args.precision in ("f32", "f16") else None)
     # lattice updates per second if every launch moved exactly its algorithmic
     # bytes at the measured copy bandwidth (one pass over the state per launch)
     glups_bound = peak / (bpu / spl)

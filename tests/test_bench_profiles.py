@@ -22,6 +22,14 @@ def test_committed_profile_matches_current_kernel(steps_per_launch, edge):
     assert 0.9 * algorithmic < traffic < 1.1 * algorithmic
 
 
+@pytest.mark.parametrize("edge", [256, 512])
+def test_committed_fp16_profile_matches_current_kernel(edge):
+    traffic = bench._traffic(bench._kernel_sha(2), name=bench._profile_name(2, edge, "f16"))
+    assert traffic is not None, "kernel source changed since its profile was captured"
+    algorithmic = 29.0 * edge ** 3  # FP16 populations read and written once per launch, plus the class byte
+    assert 0.85 * algorithmic < traffic < 1.1 * algorithmic
+
+
 def test_committed_ensemble_profile_matches_current_kernel():
     traffic = bench._traffic(bench._kernel_sha(2), name="batch_update2_d3q7_f32_ensemble64.md")
     assert traffic is not None, "kernel source changed since its profile was captured"
