@@ -691,7 +691,9 @@ def run_sweep(args):
             launch_ms = a.elapsed_time(b) / 64 * info.steps_per_launch
             achieved = info.bytes_per_update * cells / (launch_ms * 1e-3) / 1e9
             roofline[prec] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                              "frac": achieved / peak, "traffic": None,
+                              "frac": achieved / peak,
+                              "traffic": (_traffic(_kernel_sha(2), 2, 512, name=_profile_name(2, 512, prec))
+                                          if info.steps_per_launch == 2 else None),
                               "kernel": "update2_slab, %d steps/launch, %d-row slabs (%s storage)"
                                         % (info.steps_per_launch, info.two_step_rows, prec),
                               "bytes_per_cell_per_launch": info.bytes_per_update,
